@@ -1,0 +1,146 @@
+/*
+ * gemmfip.h -- C ABI of the GB300 (sm_103a) fused-in-packing GEMM library.
+ *
+ * Operation (GEMMFIP, Sec. 2.1: the gemm C := A B + C, with A m x k, B k x n, C m x n;
+ * extended to the BLAS dgemm/sgemm interface of Sec. 1):
+ *
+ *     C := alpha * op(A) * op(B) + beta * C,      op(X) = X ('N') or X^T ('T', 'C')
+ *
+ * All matrices are column-major with leading dimensions (element (i, j) of a matrix with
+ * leading dimension ld sits at index i + j*ld).  op(A) is m x k, op(B) is k x n.
+ *
+ * Method (Sec. 3.1-3.2, Alg. 1): every operand panel that is reused is packed into a
+ * contiguous tile layout the first time a CTA computes with it, in the same pass ("fused-in
+ * packing"); later CTAs load the packed copy.  Which operands are worth packing follows the
+ * option table of Sec. 3.3 (pack A only if the result has more than one tile column, pack
+ * B only if it has more than one tile row).  The two comparison variants of Sec. 2.3-2.4
+ * are exported as well: a direct-strided kernel that never packs (the SUP path) and a
+ * pack-then-compute pair of launches (the conventional path).  All three produce
+ * bit-identical results for the same arguments on the same GPU.
+ *
+ * Pointers: A, B and C are DEVICE pointers owned by the caller; A and B are only read;
+ * only the m x n logical region of C is written (rows m..ldc-1 are never touched).  Calls
+ * are asynchronous on the handle's stream.
+ *
+ * Return codes: 0 on success; a negative value -p names the first invalid argument by its
+ * 1-based position in the reference-BLAS argument list
+ *     (transa=1, transb=2, m=3, n=4, k=5, alpha=6, A=7, lda=8, B=9, ldb=10, beta=11, C=12,
+ *      ldc=13),
+ * exactly as xerbla would report it; positive values are the GFIP_ERR_* runtime errors.
+ * On any nonzero return nothing has been launched and C is unchanged.
+ *
+ * Quick returns (reference-BLAS rules): m == 0 or n == 0, or (alpha == 0 or k == 0) and
+ * beta == 1, return 0 with nothing launched; alpha == 0 or k == 0 scales C by beta
+ * without reading A or B; beta == 0 never reads C, so NaN/Inf in C do not propagate.
+ *
+ * Threading: a handle is used by one host thread at a time.  A workspace belongs to one
+ * handle; two handles must not share one.
+ */
+#ifndef GEMMFIP_H
+#define GEMMFIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfip_handle_s *gfip_handle_t;
+
+/* Runtime error codes (positive). */
+#define GFIP_OK 0
+#define GFIP_ERR_HANDLE 1       /* null or destroyed handle                                */
+#define GFIP_ERR_CUDA 2         /* a CUDA runtime call failed (launch, memset, query)      */
+#define GFIP_ERR_WORKSPACE 3    /* no workspace set, or smaller than gfip_workspace_size() */
+#define GFIP_ERR_NULLPTR 4      /* A, B or C is NULL although it would be accessed         */
+#define GFIP_ERR_DEVICE 5       /* the current device is not an sm_103 GPU                 */
+#define GFIP_ERR_SIZE 6         /* a dimension or leading dimension exceeds 2^31 - 1       */
+#define GFIP_ERR_ARG 7          /* an invalid value for a non-BLAS argument                */
+
+/* Device status bits, reported by gfip_get_status(). */
+#define GFIP_STATUS_BAD_SEGMENT 0x1u   /* a split tile saw more partial sums than planned */
+
+/* Pack policies for gfip_set_pack_policy(). */
+#define GFIP_PACK_AUTO 0        /* Sec. 3.3 option table: pack A iff > 1 tile column, B iff > 1 tile row */
+#define GFIP_PACK_NONE 1        /* never pack (the fused kernel then equals the direct variant)          */
+#define GFIP_PACK_A 2           /* pack A panels only                                                   */
+#define GFIP_PACK_B 3           /* pack B panels only                                                   */
+#define GFIP_PACK_BOTH 4        /* pack both operands regardless of reuse                               */
+
+/* Creates a handle bound to the CURRENT CUDA device; its stream is the legacy default
+ * stream until gfip_set_stream().  Returns GFIP_ERR_DEVICE if that device is not sm_103,
+ * GFIP_ERR_CUDA if the device cannot be queried. */
+int gfip_create(gfip_handle_t *handle);
+
+/* Destroys a handle.  Does not free the caller's workspace.  Pending work is not waited for. */
+int gfip_destroy(gfip_handle_t handle);
+
+/* Sets the stream (a cudaStream_t passed as void*; NULL = legacy default stream) on which
+ * every later call of this handle is enqueued. */
+int gfip_set_stream(gfip_handle_t handle, void *stream);
+
+/* Bytes of device workspace a call with these arguments needs on this handle
+ * (elem_bytes: 8 for the d-routines, 4 for the s-routines).  The figure includes the packed
+ * copies of both operands (Sec. 2.1, "packed memory"), the per-panel ready words and the
+ * partial sums of split tiles.  Returns 0 for invalid arguments. */
+size_t gfip_workspace_size(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
+                           int64_t k, int elem_bytes);
+
+/* Hands the handle a caller-owned device buffer (16-byte aligned) of `bytes` bytes.  The
+ * library never allocates device memory itself.  The buffer must stay valid, and must not be
+ * used by anything else, until the last call that uses it has completed on the stream.  The
+ * first call after this one clears the buffer's control words (an asynchronous memset on the
+ * handle's stream). */
+int gfip_set_workspace(gfip_handle_t handle, void *dev_ptr, size_t bytes);
+
+/* Chooses which operands the fused routines pack (GFIP_PACK_*); testing and tuning aid.
+ * The result bits do not depend on the policy. */
+int gfip_set_pack_policy(gfip_handle_t handle, int policy);
+
+/* Fused-in-packing GEMM (the method of Sec. 3.2), FP64 and FP32. */
+int gfip_dgemm(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n, int64_t k,
+               double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
+               double beta, double *C, int64_t ldc);
+int gfip_sgemm(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n, int64_t k,
+               float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+               float beta, float *C, int64_t ldc);
+
+/* Direct-strided comparison variant: never packs; every CTA reads the raw strided operands
+ * (the SUP path of Sec. 2.3).  Needs a workspace only for split-tile partial sums. */
+int gfip_dgemm_direct(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
+                      int64_t k, double alpha, const double *A, int64_t lda, const double *B,
+                      int64_t ldb, double beta, double *C, int64_t ldc);
+int gfip_sgemm_direct(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
+                      int64_t k, float alpha, const float *A, int64_t lda, const float *B,
+                      int64_t ldb, float beta, float *C, int64_t ldc);
+
+/* Pack-then-compute comparison variant: a pack kernel copies both operands into the packed
+ * layout, then the GEMM kernel reads only packed tiles (the conventional path of Sec. 2.1,
+ * Fig. 1).  Two launches on the handle's stream. */
+int gfip_dgemm_pack_then_compute(gfip_handle_t handle, char transa, char transb, int64_t m,
+                                 int64_t n, int64_t k, double alpha, const double *A,
+                                 int64_t lda, const double *B, int64_t ldb, double beta,
+                                 double *C, int64_t ldc);
+int gfip_sgemm_pack_then_compute(gfip_handle_t handle, char transa, char transb, int64_t m,
+                                 int64_t n, int64_t k, float alpha, const float *A,
+                                 int64_t lda, const float *B, int64_t ldb, float beta,
+                                 float *C, int64_t ldc);
+
+/* Waits for the handle's stream, then returns the OR of the device status bits
+ * (GFIP_STATUS_*) raised since the previous call of this function, and clears them.
+ * Needs a workspace. */
+int gfip_get_status(gfip_handle_t handle, uint32_t *status);
+
+/* Number of kernel launches the most recent GEMM call of this handle enqueued (0 for a quick
+ * return), and the grid size of its GEMM kernel. */
+int gfip_last_launch_info(gfip_handle_t handle, int *launches, int *grid);
+
+/* Static description of a return code. */
+const char *gfip_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEMMFIP_H */

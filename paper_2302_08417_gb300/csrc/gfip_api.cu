@@ -1,0 +1,509 @@
+// gfip_api.cu -- C ABI of the fused-in-packing GEMM: argument checks (reference-BLAS
+// codes), quick returns, the launch plan (tile grid, schedule, pack modes), the workspace
+// layout, and the launches.  See include/gemmfip.h for the contract.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gemmfip.h"
+#include "gfip_internal.h"
+
+namespace {
+
+constexpr uint32_t kMagic = 0x67666970u;  // "gfip"
+constexpr size_t kAlign = 256;
+constexpr size_t kHeader = 256;             // status word and spare
+constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
+
+struct Handle {
+    uint32_t magic = kMagic;
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    // Bytes at the start of the workspace that hold only control words (zeros, or words a
+    // kernel of this handle tagged with an older epoch).  Data never lives below this mark.
+    size_t ctrl_bytes = 0;
+    unsigned int epoch = 0;
+    int pack_policy = GFIP_PACK_AUTO;
+    int last_launches = 0;
+    int last_grid = 0;
+    int bps_f64 = 0;
+    int bps_f32 = 0;
+};
+
+Handle *get(gfip_handle_t h)
+{
+    Handle *p = reinterpret_cast<Handle *>(h);
+    if (p == nullptr || p->magic != kMagic) return nullptr;
+    return p;
+}
+
+size_t round_up(size_t x, size_t a)
+{
+    return (x + a - 1) / a * a;
+}
+
+bool is_trans_char(char t)
+{
+    return t == 'N' || t == 'n' || t == 'T' || t == 't' || t == 'C' || t == 'c';
+}
+
+bool is_notrans(char t)
+{
+    return t == 'N' || t == 'n';
+}
+
+// Reference-BLAS argument check (xerbla positions, negated).
+int check_args(char transa, char transb, int64_t m, int64_t n, int64_t k, int64_t lda,
+               int64_t ldb, int64_t ldc)
+{
+    if (!is_trans_char(transa)) return -1;
+    if (!is_trans_char(transb)) return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (k < 0) return -5;
+    const int64_t rows_a = is_notrans(transa) ? m : k;
+    const int64_t rows_b = is_notrans(transb) ? k : n;
+    if (lda < std::max<int64_t>(1, rows_a)) return -8;
+    if (ldb < std::max<int64_t>(1, rows_b)) return -10;
+    if (ldc < std::max<int64_t>(1, m)) return -13;
+    return 0;
+}
+
+enum class Variant { Fused, Direct, PackThenCompute };
+
+template <typename T> struct Plan {
+    int mt = 0, nt = 0, kt = 0, tiles = 0;
+    int grid = 0, dp_tiles = 0;
+    int64_t sk_iters = 0;
+    int mode_a = gfip::MODE_RAW, mode_b = gfip::MODE_RAW;
+    // workspace layout (byte offsets from the workspace base)
+    size_t ctrl_needed = 0;
+    size_t off_count = 0, off_state_a = 0, off_state_b = 0;
+    size_t data_partial = 0, data_pack_a = 0, data_pack_b = 0, data_bytes = 0;
+};
+
+template <typename T> int blocks_per_sm(Handle *h)
+{
+    int &slot = (sizeof(T) == 8) ? h->bps_f64 : h->bps_f32;
+    if (slot == 0) slot = gfip::gemm_blocks_per_sm<T>();
+    return slot;
+}
+
+template <typename T>
+Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
+{
+    using Cfg = gfip::TileCfg<T>;
+    Plan<T> pl;
+    pl.mt = (m + Cfg::BM - 1) / Cfg::BM;
+    pl.nt = (n + Cfg::BN - 1) / Cfg::BN;
+    pl.kt = (k + Cfg::BK - 1) / Cfg::BK;
+    pl.tiles = pl.mt * pl.nt;
+
+    // Schedule: data-parallel waves of whole tiles, then the remaining tiles (the partial
+    // wave plus one full wave) split evenly along k over all CTAs.
+    const int bps = std::max(1, blocks_per_sm<T>(h));
+    const int full = h->sms * bps;
+    const int64_t total_iters = (int64_t)pl.tiles * pl.kt;
+    if (pl.tiles % full == 0) {
+        pl.grid = full;
+        pl.dp_tiles = pl.tiles;
+        pl.sk_iters = 0;
+    } else if (pl.tiles < full) {
+        pl.grid = static_cast<int>(std::min<int64_t>(full, total_iters));
+        pl.dp_tiles = 0;
+        pl.sk_iters = total_iters;
+    } else {
+        const int rem = pl.tiles % full;
+        const int sk_tiles = rem + full;
+        pl.grid = full;
+        pl.dp_tiles = pl.tiles - sk_tiles;
+        pl.sk_iters = (int64_t)sk_tiles * pl.kt;
+    }
+
+    // Which operands are packed, and how (Sec. 3.3 option table for the fused variant).
+    switch (v) {
+    case Variant::Direct:
+        pl.mode_a = pl.mode_b = gfip::MODE_RAW;
+        break;
+    case Variant::PackThenCompute:
+        pl.mode_a = pl.mode_b = gfip::MODE_PACKED;
+        break;
+    case Variant::Fused:
+        switch (h->pack_policy) {
+        case GFIP_PACK_NONE:
+            pl.mode_a = pl.mode_b = gfip::MODE_RAW;
+            break;
+        case GFIP_PACK_A:
+            pl.mode_a = gfip::MODE_FIP;
+            pl.mode_b = gfip::MODE_RAW;
+            break;
+        case GFIP_PACK_B:
+            pl.mode_a = gfip::MODE_RAW;
+            pl.mode_b = gfip::MODE_FIP;
+            break;
+        case GFIP_PACK_BOTH:
+            pl.mode_a = pl.mode_b = gfip::MODE_FIP;
+            break;
+        default:  // AUTO: an A panel is reused only across tile columns, a B panel across rows
+            pl.mode_a = (pl.nt > 1) ? gfip::MODE_FIP : gfip::MODE_RAW;
+            pl.mode_b = (pl.mt > 1) ? gfip::MODE_FIP : gfip::MODE_RAW;
+            break;
+        }
+        break;
+    }
+
+    // Control region: header, arrival counters of split tiles, ready words of packed tiles.
+    size_t off = kHeader;
+    pl.off_count = off;
+    off += round_up((size_t)pl.tiles * 8, kAlign);
+    pl.off_state_a = off;
+    if (pl.mode_a == gfip::MODE_FIP) off += round_up((size_t)pl.mt * pl.kt * 8, kAlign);
+    pl.off_state_b = off;
+    if (pl.mode_b == gfip::MODE_FIP) off += round_up((size_t)pl.nt * pl.kt * 8, kAlign);
+    pl.ctrl_needed = off;
+
+    // Data region (relative to its start): partial sums, packed A, packed B.
+    size_t d = 0;
+    pl.data_partial = d;
+    if (pl.sk_iters > 0) d += round_up((size_t)pl.grid * 2 * Cfg::BM * Cfg::BN * sizeof(T), kAlign);
+    pl.data_pack_a = d;
+    if (pl.mode_a != gfip::MODE_RAW)
+        d += round_up((size_t)pl.mt * pl.kt * Cfg::BM * Cfg::BK * sizeof(T), kAlign);
+    pl.data_pack_b = d;
+    if (pl.mode_b != gfip::MODE_RAW)
+        d += round_up((size_t)pl.nt * pl.kt * Cfg::BN * Cfg::BK * sizeof(T), kAlign);
+    pl.data_bytes = d;
+    return pl;
+}
+
+template <typename T> size_t total_bytes(Handle *h, const Plan<T> &pl)
+{
+    const size_t ctrl = std::max(h->ctrl_bytes, round_up(pl.ctrl_needed, kCtrlGranule));
+    return ctrl + pl.data_bytes;
+}
+
+bool too_big(int64_t v)
+{
+    return v > std::numeric_limits<int32_t>::max();
+}
+
+template <typename T>
+int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_t m, int64_t n,
+               int64_t k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb, T beta, T *C,
+               int64_t ldc)
+{
+    const int info = check_args(transa, transb, m, n, k, lda, ldb, ldc);
+    if (info != 0) return info;
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    h->last_launches = 0;
+    h->last_grid = 0;
+    if (m == 0 || n == 0) return GFIP_OK;
+    const bool use_ab = !(alpha == T(0) || k == 0);
+    if (!use_ab && beta == T(1)) return GFIP_OK;
+    if (too_big(m) || too_big(n) || too_big(k) || too_big(lda) || too_big(ldb) || too_big(ldc))
+        return GFIP_ERR_SIZE;
+    if (C == nullptr) return GFIP_ERR_NULLPTR;
+    if (!use_ab) {
+        if (gfip::launch_scale<T>(C, ldc, (int)m, (int)n, beta, h->stream) != cudaSuccess)
+            return GFIP_ERR_CUDA;
+        h->last_launches = 1;
+        return GFIP_OK;
+    }
+    if (A == nullptr || B == nullptr) return GFIP_ERR_NULLPTR;
+
+    Plan<T> pl = make_plan<T>(h, v, (int)m, (int)n, (int)k);
+    if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
+    if (total_bytes(h, pl) > h->ws_bytes) return GFIP_ERR_WORKSPACE;
+
+    // Grow the control region if this plan needs more of it; the new part may hold data of
+    // earlier calls, so it is cleared (stream-ordered after them).
+    const size_t ctrl_want = round_up(pl.ctrl_needed, kCtrlGranule);
+    if (ctrl_want > h->ctrl_bytes) {
+        if (cudaMemsetAsync(h->ws + h->ctrl_bytes, 0, ctrl_want - h->ctrl_bytes, h->stream) !=
+            cudaSuccess)
+            return GFIP_ERR_CUDA;
+        h->ctrl_bytes = ctrl_want;
+    }
+    // Epoch tags make the ready words and counters of earlier calls read as "unclaimed".
+    if (h->epoch == 0xffffffffu) {
+        if (cudaMemsetAsync(h->ws, 0, h->ctrl_bytes, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
+        h->epoch = 0;
+    }
+    h->epoch += 1;
+
+    unsigned char *data = h->ws + h->ctrl_bytes;
+    gfip::GemmParams<T> p{};
+    p.A = A;
+    p.B = B;
+    p.C = C;
+    p.lda = lda;
+    p.ldb = ldb;
+    p.ldc = ldc;
+    p.m = (int)m;
+    p.n = (int)n;
+    p.k = (int)k;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.a_contig_m = is_notrans(transa) ? 1 : 0;
+    p.b_contig_n = is_notrans(transb) ? 0 : 1;
+    p.mt = pl.mt;
+    p.nt = pl.nt;
+    p.kt = pl.kt;
+    p.tiles = pl.tiles;
+    p.grid = pl.grid;
+    p.dp_tiles = pl.dp_tiles;
+    p.sk_iters = pl.sk_iters;
+    p.mode_a = pl.mode_a;
+    p.mode_b = pl.mode_b;
+    p.state_a = reinterpret_cast<unsigned long long *>(h->ws + pl.off_state_a);
+    p.state_b = reinterpret_cast<unsigned long long *>(h->ws + pl.off_state_b);
+    p.tile_count = reinterpret_cast<unsigned long long *>(h->ws + pl.off_count);
+    p.pack_a = reinterpret_cast<T *>(data + pl.data_pack_a);
+    p.pack_b = reinterpret_cast<T *>(data + pl.data_pack_b);
+    p.partial = reinterpret_cast<T *>(data + pl.data_partial);
+    p.status = reinterpret_cast<unsigned int *>(h->ws);
+    p.epoch = h->epoch;
+
+    int launches = 0;
+    if (v == Variant::PackThenCompute) {
+        gfip::PackParams<T> pp{};
+        pp.A = A;
+        pp.B = B;
+        pp.lda = lda;
+        pp.ldb = ldb;
+        pp.m = p.m;
+        pp.n = p.n;
+        pp.k = p.k;
+        pp.a_contig_m = p.a_contig_m;
+        pp.b_contig_n = p.b_contig_n;
+        pp.mt = pl.mt;
+        pp.nt = pl.nt;
+        pp.kt = pl.kt;
+        pp.pack_a = p.pack_a;
+        pp.pack_b = p.pack_b;
+        if (gfip::launch_pack<T>(pp, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
+        ++launches;
+    }
+    if (gfip::launch_gemm<T>(p, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
+    ++launches;
+    h->last_launches = launches;
+    h->last_grid = pl.grid;
+    return GFIP_OK;
+}
+
+template <typename T>
+size_t workspace_size_impl(Handle *h, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                           Variant v)
+{
+    if (check_args(transa, transb, m, n, k, is_notrans(transa) ? std::max<int64_t>(1, m)
+                                                              : std::max<int64_t>(1, k),
+                   is_notrans(transb) ? std::max<int64_t>(1, k) : std::max<int64_t>(1, n),
+                   std::max<int64_t>(1, m)) != 0)
+        return 0;
+    if (too_big(m) || too_big(n) || too_big(k)) return 0;
+    if (m == 0 || n == 0 || k == 0) return round_up(kHeader, kCtrlGranule);
+    const Plan<T> pl = make_plan<T>(h, v, (int)m, (int)n, (int)k);
+    return total_bytes(h, pl);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gfip_create(gfip_handle_t *handle)
+{
+    if (handle == nullptr) return GFIP_ERR_ARG;
+    *handle = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GFIP_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return GFIP_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return GFIP_ERR_DEVICE;
+    Handle *h = new (std::nothrow) Handle();
+    if (h == nullptr) return GFIP_ERR_ARG;
+    h->device = dev;
+    h->sms = prop.multiProcessorCount;
+    *handle = reinterpret_cast<gfip_handle_t>(h);
+    return GFIP_OK;
+}
+
+int gfip_destroy(gfip_handle_t handle)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    h->magic = 0;
+    delete h;
+    return GFIP_OK;
+}
+
+int gfip_set_stream(gfip_handle_t handle, void *stream)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    return GFIP_OK;
+}
+
+size_t gfip_workspace_size(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
+                           int64_t k, int elem_bytes)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return 0;
+    // The largest of the three variants, so one workspace serves all of them.
+    if (elem_bytes == 8) {
+        size_t s = 0;
+        for (Variant v : {Variant::Fused, Variant::Direct, Variant::PackThenCompute}) {
+            const int saved = h->pack_policy;
+            if (v == Variant::Fused) h->pack_policy = GFIP_PACK_BOTH;
+            s = std::max(s, workspace_size_impl<double>(h, transa, transb, m, n, k, v));
+            h->pack_policy = saved;
+        }
+        return s;
+    }
+    if (elem_bytes == 4) {
+        size_t s = 0;
+        for (Variant v : {Variant::Fused, Variant::Direct, Variant::PackThenCompute}) {
+            const int saved = h->pack_policy;
+            if (v == Variant::Fused) h->pack_policy = GFIP_PACK_BOTH;
+            s = std::max(s, workspace_size_impl<float>(h, transa, transb, m, n, k, v));
+            h->pack_policy = saved;
+        }
+        return s;
+    }
+    return 0;
+}
+
+int gfip_set_workspace(gfip_handle_t handle, void *dev_ptr, size_t bytes)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    if (dev_ptr != nullptr && (reinterpret_cast<uintptr_t>(dev_ptr) % 16) != 0) return GFIP_ERR_ARG;
+    h->ws = reinterpret_cast<unsigned char *>(dev_ptr);
+    h->ws_bytes = dev_ptr ? bytes : 0;
+    h->ctrl_bytes = 0;
+    h->epoch = 0;
+    return GFIP_OK;
+}
+
+int gfip_set_pack_policy(gfip_handle_t handle, int policy)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    if (policy < GFIP_PACK_AUTO || policy > GFIP_PACK_BOTH) return GFIP_ERR_ARG;
+    h->pack_policy = policy;
+    return GFIP_OK;
+}
+
+int gfip_dgemm(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n, int64_t k,
+               double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
+               double beta, double *C, int64_t ldc)
+{
+    return gemm_entry<double>(handle, Variant::Fused, transa, transb, m, n, k, alpha, A, lda, B,
+                              ldb, beta, C, ldc);
+}
+
+int gfip_sgemm(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n, int64_t k,
+               float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
+               float *C, int64_t ldc)
+{
+    return gemm_entry<float>(handle, Variant::Fused, transa, transb, m, n, k, alpha, A, lda, B,
+                             ldb, beta, C, ldc);
+}
+
+int gfip_dgemm_direct(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
+                      int64_t k, double alpha, const double *A, int64_t lda, const double *B,
+                      int64_t ldb, double beta, double *C, int64_t ldc)
+{
+    return gemm_entry<double>(handle, Variant::Direct, transa, transb, m, n, k, alpha, A, lda,
+                              B, ldb, beta, C, ldc);
+}
+
+int gfip_sgemm_direct(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
+                      int64_t k, float alpha, const float *A, int64_t lda, const float *B,
+                      int64_t ldb, float beta, float *C, int64_t ldc)
+{
+    return gemm_entry<float>(handle, Variant::Direct, transa, transb, m, n, k, alpha, A, lda, B,
+                             ldb, beta, C, ldc);
+}
+
+int gfip_dgemm_pack_then_compute(gfip_handle_t handle, char transa, char transb, int64_t m,
+                                 int64_t n, int64_t k, double alpha, const double *A,
+                                 int64_t lda, const double *B, int64_t ldb, double beta,
+                                 double *C, int64_t ldc)
+{
+    return gemm_entry<double>(handle, Variant::PackThenCompute, transa, transb, m, n, k, alpha, A,
+                              lda, B, ldb, beta, C, ldc);
+}
+
+int gfip_sgemm_pack_then_compute(gfip_handle_t handle, char transa, char transb, int64_t m,
+                                 int64_t n, int64_t k, float alpha, const float *A, int64_t lda,
+                                 const float *B, int64_t ldb, float beta, float *C,
+                                 int64_t ldc)
+{
+    return gemm_entry<float>(handle, Variant::PackThenCompute, transa, transb, m, n, k, alpha, A,
+                             lda, B, ldb, beta, C, ldc);
+}
+
+int gfip_get_status(gfip_handle_t handle, uint32_t *status)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    if (status == nullptr) return GFIP_ERR_ARG;
+    if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
+    *status = 0;
+    if (h->ctrl_bytes == 0) return GFIP_OK;  // no kernel has written a status yet
+    uint32_t v = 0;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
+    if (cudaMemcpy(&v, h->ws, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GFIP_ERR_CUDA;
+    if (cudaMemsetAsync(h->ws, 0, sizeof(v), h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
+    *status = v;
+    return GFIP_OK;
+}
+
+int gfip_last_launch_info(gfip_handle_t handle, int *launches, int *grid)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    if (launches) *launches = h->last_launches;
+    if (grid) *grid = h->last_grid;
+    return GFIP_OK;
+}
+
+const char *gfip_error_string(int code)
+{
+    if (code < 0) {
+        switch (code) {
+        case -1: return "invalid argument 1 (transa)";
+        case -2: return "invalid argument 2 (transb)";
+        case -3: return "invalid argument 3 (m < 0)";
+        case -4: return "invalid argument 4 (n < 0)";
+        case -5: return "invalid argument 5 (k < 0)";
+        case -8: return "invalid argument 8 (lda < max(1, rows of A))";
+        case -10: return "invalid argument 10 (ldb < max(1, rows of B))";
+        case -13: return "invalid argument 13 (ldc < max(1, m))";
+        default: return "invalid argument";
+        }
+    }
+    switch (code) {
+    case GFIP_OK: return "success";
+    case GFIP_ERR_HANDLE: return "invalid handle";
+    case GFIP_ERR_CUDA: return "CUDA runtime error";
+    case GFIP_ERR_WORKSPACE: return "workspace missing or too small";
+    case GFIP_ERR_NULLPTR: return "null matrix pointer";
+    case GFIP_ERR_DEVICE: return "device is not sm_103";
+    case GFIP_ERR_SIZE: return "dimension exceeds 2^31-1";
+    case GFIP_ERR_ARG: return "invalid argument value";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// gfip_internal.h -- host/device shared definitions of the fused-in-packing GEMM library.
+// Not part of the public ABI (that is include/gemmfip.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gfip {
+
+// Where an operand's tiles come from in one launch of the GEMM kernel.
+enum OperandMode : int {
+    MODE_RAW = 0,     // always read the raw strided operand (direct variant, SUP analog)
+    MODE_PACKED = 1,  // always read the packed copy, written beforehand by the pack kernel
+    MODE_FIP = 2,     // fused: the first CTA to touch a (panel, k-block) packs it, later
+                      // touches read the packed copy (Sec. 3.1 Alg. 1, Sec. 3.2, Sec. 3.5)
+};
+
+// Tile shape of one element type.  The CTA computes a BM x BN tile of C, stepping through
+// k in blocks of BK; 256 threads each own a (2*CH) x (2*CH) register micro-tile.
+template <typename T> struct TileCfg;
+
+template <> struct TileCfg<double> {
+    static constexpr int BM = 64, BN = 64, BK = 16, THREADS = 256, STAGES = 4, MIN_BLOCKS = 2;
+};
+template <> struct TileCfg<float> {
+    static constexpr int BM = 128, BN = 128, BK = 16, THREADS = 256, STAGES = 3, MIN_BLOCKS = 1;
+};
+
+// Everything one launch of the GEMM kernel needs.  Plain data, passed by value.
+template <typename T> struct GemmParams {
+    const T *A;
+    const T *B;
+    T *C;
+    int64_t lda, ldb, ldc;
+    int m, n, k;
+    T alpha, beta;
+    int a_contig_m;   // 1: op(A)[i,p] = A[i + p*lda] (transa 'N'); 0: A[p + i*lda]
+    int b_contig_n;   // 1: op(B)[p,j] = B[j + p*ldb] (transb 'T'); 0: B[p + j*ldb]
+    int mt, nt, kt;   // tile counts along m, n and k
+    int tiles;        // mt * nt
+    int grid;         // persistent CTAs
+    int dp_tiles;     // tiles [0, dp_tiles) are data-parallel: tile t runs on CTA t % grid
+    int64_t sk_iters; // (tiles - dp_tiles) * kt iterations split evenly over the CTAs
+    int mode_a, mode_b;
+    unsigned long long *state_a;     // [mt * kt] epoch-tagged ready words of packed A
+    unsigned long long *state_b;     // [nt * kt] same for B
+    unsigned long long *tile_count;  // [tiles] epoch-tagged arrival counters of split tiles
+    T *pack_a;                       // [mt * kt] tiles of BM * BK elements
+    T *pack_b;                       // [nt * kt] tiles of BN * BK elements
+    T *partial;                      // [grid * 2] slots of BM * BN elements
+    unsigned int *status;            // device status bits (GFIP_STATUS_*)
+    unsigned int epoch;              // tag of this call (>= 1)
+};
+
+// Parameters of the pack kernel of the pack-then-compute variant.
+template <typename T> struct PackParams {
+    const T *A;
+    const T *B;
+    int64_t lda, ldb;
+    int m, n, k;
+    int a_contig_m, b_contig_n;
+    int mt, nt, kt;
+    T *pack_a;
+    T *pack_b;
+};
+
+// Launchers (defined per element type in gfip_f64.cu / gfip_f32.cu).
+template <typename T> cudaError_t launch_gemm(const GemmParams<T> &p, cudaStream_t s);
+template <typename T> cudaError_t launch_pack(const PackParams<T> &p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale(T *C, int64_t ldc, int m, int n, T beta, cudaStream_t s);
+// CTAs of the GEMM kernel that fit on one SM at once.
+template <typename T> int gemm_blocks_per_sm();
+
+}  // namespace gfip

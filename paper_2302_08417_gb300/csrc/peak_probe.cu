@@ -1,0 +1,212 @@
+// peak_probe.cu -- measures the arithmetic peaks the GEMM roofline is taken against:
+// FP64 DFMA, FP64 mma.sync (DMMA) shapes, FP32 FFMA, and the SM clock seen meanwhile.
+// Prints one JSON object on stdout.  Standalone executable; not part of the library.
+//
+// Each kernel runs independent multiply-add chains (no memory traffic in the timed loop)
+// and writes one value per thread at the end so the compiler keeps the arithmetic.
+#include <cstdio>
+#include <cstdlib>
+#include <cuda_runtime.h>
+
+#define CK(x)                                                                          \
+    do {                                                                               \
+        cudaError_t e_ = (x);                                                          \
+        if (e_ != cudaSuccess) {                                                       \
+            fprintf(stderr, "CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, \
+                    __LINE__);                                                         \
+            exit(1);                                                                   \
+        }                                                                              \
+    } while (0)
+
+constexpr int CHAINS = 8;
+
+__global__ void dfma_kernel(double *out, int iters, double a, double b)
+{
+    double acc[CHAINS];
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) acc[c] = threadIdx.x * 1e-9 + c;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < CHAINS; ++c) acc[c] = fma(acc[c], a, b);
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) s += acc[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void ffma_kernel(float *out, int iters, float a, float b)
+{
+    float acc[CHAINS * 2];
+#pragma unroll
+    for (int c = 0; c < CHAINS * 2; ++c) acc[c] = threadIdx.x * 1e-6f + c;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < CHAINS * 2; ++c) acc[c] = fmaf(acc[c], a, b);
+    }
+    float s = 0;
+#pragma unroll
+    for (int c = 0; c < CHAINS * 2; ++c) s += acc[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// mma.sync m8n8k4 f64: A 8x4 (1 elem/thread), B 4x8 (1 elem/thread), C 8x8 (2 elems/thread)
+__global__ void dmma_m8n8k4_kernel(double *out, int iters, double a, double b)
+{
+    double acc[4][2];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { acc[c][0] = threadIdx.x; acc[c][1] = c; }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 "
+                         "{%0, %1}, {%2}, {%3}, {%0, %1};\n"
+                         : "+d"(acc[c][0]), "+d"(acc[c][1])
+                         : "d"(a), "d"(b));
+        }
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s += acc[c][0] + acc[c][1];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// mma.sync m16n8k4 f64: A 16x4 (2/thread), B 4x8 (1/thread), C 16x8 (4/thread)
+__global__ void dmma_m16n8k4_kernel(double *out, int iters, double a, double b)
+{
+    double acc[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[c][r] = threadIdx.x + r + c;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            asm volatile("mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 "
+                         "{%0, %1, %2, %3}, {%4, %5}, {%6}, {%0, %1, %2, %3};\n"
+                         : "+d"(acc[c][0]), "+d"(acc[c][1]), "+d"(acc[c][2]), "+d"(acc[c][3])
+                         : "d"(a), "d"(b), "d"(b));
+        }
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s += acc[c][0] + acc[c][1] + acc[c][2] + acc[c][3];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// mma.sync m16n8k16 f64: A 16x16 (8/thread), B 16x8 (4/thread), C 16x8 (4/thread)
+__global__ void dmma_m16n8k16_kernel(double *out, int iters, double a, double b)
+{
+    double acc[2][4];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[c][r] = threadIdx.x + r + c;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            asm volatile("mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 "
+                         "{%0, %1, %2, %3}, {%4, %5, %6, %7, %8, %9, %10, %11}, "
+                         "{%12, %13, %14, %15}, {%0, %1, %2, %3};\n"
+                         : "+d"(acc[c][0]), "+d"(acc[c][1]), "+d"(acc[c][2]), "+d"(acc[c][3])
+                         : "d"(a), "d"(a), "d"(a), "d"(a), "d"(a), "d"(a), "d"(a), "d"(a),
+                           "d"(b), "d"(b), "d"(b), "d"(b));
+        }
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) s += acc[c][0] + acc[c][1] + acc[c][2] + acc[c][3];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// Reads %clock64 and %globaltimer across a busy loop to estimate the SM clock.
+__global__ void clock_kernel(unsigned long long *out, int iters, double a)
+{
+    unsigned long long c0 = clock64(), t0, t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    double x = threadIdx.x;
+    for (int i = 0; i < iters; ++i) x = fma(x, a, 1e-9);
+    unsigned long long c1 = clock64();
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = c1 - c0;
+        out[2 * blockIdx.x + 1] = t1 - t0;
+    }
+    if (x == 12345.0) out[0] = 0;
+}
+
+template <typename K>
+static double time_ms(K launch, int reps)
+{
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    launch();
+    CK(cudaDeviceSynchronize());
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        CK(cudaEventRecord(e0));
+        launch();
+        CK(cudaEventRecord(e1));
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) best = ms;
+    }
+    CK(cudaGetLastError());
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+int main(int argc, char **argv)
+{
+    int dev = 0;
+    CK(cudaSetDevice(dev));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, dev));
+    int sms = prop.multiProcessorCount;
+    int clk_khz = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    int iters = argc > 1 ? atoi(argv[1]) : 4096;
+
+    const int threads = 256;
+    const int blocks = sms * 8;
+    size_t n = (size_t)blocks * threads;
+    double *dout;
+    CK(cudaMalloc(&dout, n * sizeof(double) * 2));
+    unsigned long long *cout;
+    CK(cudaMalloc(&cout, 2 * sizeof(unsigned long long) * sms));
+
+    double dfma_ms = time_ms([&] { dfma_kernel<<<blocks, threads>>>(dout, iters, 1.0000001, 1e-7); }, 5);
+    double dfma_tf = 2.0 * CHAINS * (double)iters * n / (dfma_ms * 1e-3) / 1e12;
+
+    double ffma_ms = time_ms([&] { ffma_kernel<<<blocks, threads>>>((float *)dout, iters * 8, 1.0000001f, 1e-7f); }, 5);
+    double ffma_tf = 2.0 * CHAINS * 2 * (double)iters * 8 * n / (ffma_ms * 1e-3) / 1e12;
+
+    // warps in flight: blocks*threads/32 ; each mma does 2*M*N*K flops per warp
+    double warps = (double)n / 32.0;
+    double d884_ms = time_ms([&] { dmma_m8n8k4_kernel<<<blocks, threads>>>(dout, iters, 1.0000001, 1e-7); }, 5);
+    double d884_tf = 2.0 * 8 * 8 * 4 * 4.0 * iters * warps / (d884_ms * 1e-3) / 1e12;
+    double d1684_ms = time_ms([&] { dmma_m16n8k4_kernel<<<blocks, threads>>>(dout, iters, 1.0000001, 1e-7); }, 5);
+    double d1684_tf = 2.0 * 16 * 8 * 4 * 4.0 * iters * warps / (d1684_ms * 1e-3) / 1e12;
+    double d16816_ms = time_ms([&] { dmma_m16n8k16_kernel<<<blocks, threads>>>(dout, iters / 4, 1.0000001, 1e-7); }, 5);
+    double d16816_tf = 2.0 * 16 * 8 * 16 * 2.0 * (iters / 4) * warps / (d16816_ms * 1e-3) / 1e12;
+
+    clock_kernel<<<sms, 32>>>(cout, 1 << 22, 1.0000001);
+    CK(cudaDeviceSynchronize());
+    unsigned long long hc[2];
+    CK(cudaMemcpy(hc, cout, sizeof(hc), cudaMemcpyDeviceToHost));
+    double sm_mhz = hc[1] ? (double)hc[0] / (double)hc[1] * 1e3 : 0.0;
+
+    printf("{\"sms\": %d, \"l2_bytes\": %d, \"smem_per_block_optin\": %zu, "
+           "\"regs_per_sm\": %d, \"clock_attr_mhz\": %.0f, \"sm_mhz_during_probe\": %.0f, "
+           "\"dfma_tflops\": %.4f, \"ffma_tflops\": %.3f, \"dmma_m8n8k4_tflops\": %.4f, "
+           "\"dmma_m16n8k4_tflops\": %.4f, \"dmma_m16n8k16_tflops\": %.4f, "
+           "\"iters\": %d}\n",
+           sms, prop.l2CacheSize, prop.sharedMemPerBlockOptin, prop.regsPerMultiprocessor,
+           clk_khz / 1e3, sm_mhz, dfma_tf, ffma_tf, d884_tf, d1684_tf, d16816_tf, iters);
+    cudaFree(dout);
+    cudaFree(cout);
+    return 0;
+}

@@ -1,0 +1,308 @@
+"""Python binding of the C ABI in include/gemmfip.h (argument marshalling only).
+
+The functions ``gfip_*`` below have the names and argument order of the C entry points and
+take plain integers for device pointers and streams; every step of the GEMM runs in the CUDA
+library.  :class:`Handle` and :func:`gemm` add PyTorch conveniences on top: the workspace is
+a caller-owned ``torch.uint8`` CUDA tensor, the stream is torch's current stream, and
+matrices are 2-D column-major tensor views (``X.stride(0) == 1``, leading dimension
+``X.stride(1)``), exactly the storage a BLAS caller passes.
+
+There is no fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgemmfip.so")
+
+GFIP_OK = 0
+GFIP_ERR_HANDLE = 1
+GFIP_ERR_CUDA = 2
+GFIP_ERR_WORKSPACE = 3
+GFIP_ERR_NULLPTR = 4
+GFIP_ERR_DEVICE = 5
+GFIP_ERR_SIZE = 6
+GFIP_ERR_ARG = 7
+GFIP_STATUS_BAD_SEGMENT = 0x1
+
+GFIP_PACK_AUTO, GFIP_PACK_NONE, GFIP_PACK_A, GFIP_PACK_B, GFIP_PACK_BOTH = range(5)
+
+# exported symbol -> (restype, argtypes)
+_i64, _dbl, _flt, _ptr = ctypes.c_int64, ctypes.c_double, ctypes.c_float, ctypes.c_void_p
+_chr, _int, _sz = ctypes.c_char, ctypes.c_int, ctypes.c_size_t
+_GEMM_D = [_ptr, _chr, _chr, _i64, _i64, _i64, _dbl, _ptr, _i64, _ptr, _i64, _dbl, _ptr, _i64]
+_GEMM_S = [_ptr, _chr, _chr, _i64, _i64, _i64, _flt, _ptr, _i64, _ptr, _i64, _flt, _ptr, _i64]
+SIGNATURES = {
+    "gfip_create": (_int, [ctypes.POINTER(_ptr)]),
+    "gfip_destroy": (_int, [_ptr]),
+    "gfip_set_stream": (_int, [_ptr, _ptr]),
+    "gfip_workspace_size": (_sz, [_ptr, _chr, _chr, _i64, _i64, _i64, _int]),
+    "gfip_set_workspace": (_int, [_ptr, _ptr, _sz]),
+    "gfip_set_pack_policy": (_int, [_ptr, _int]),
+    "gfip_dgemm": (_int, _GEMM_D),
+    "gfip_sgemm": (_int, _GEMM_S),
+    "gfip_dgemm_direct": (_int, _GEMM_D),
+    "gfip_sgemm_direct": (_int, _GEMM_S),
+    "gfip_dgemm_pack_then_compute": (_int, _GEMM_D),
+    "gfip_sgemm_pack_then_compute": (_int, _GEMM_S),
+    "gfip_get_status": (_int, [_ptr, ctypes.POINTER(ctypes.c_uint32)]),
+    "gfip_last_launch_info": (_int, [_ptr, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "gfip_error_string": (ctypes.c_char_p, [_int]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GemmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} (code {code})")
+
+
+def load(path: str = LIB_PATH):
+    """Loads libgemmfip.so (built by ``paper_2302_08417_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{path} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return load().gfip_error_string(code).decode()
+
+
+def _b(c: str) -> bytes:
+    return c.encode() if isinstance(c, str) else c
+
+
+# ---- thin wrappers with the C names (pointers and streams are ints) -------------------
+
+def gfip_create() -> int:
+    h = _ptr()
+    rc = load().gfip_create(ctypes.byref(h))
+    if rc != GFIP_OK:
+        raise GemmError(rc, "gfip_create")
+    return h.value
+
+
+def gfip_destroy(handle: int) -> int:
+    return load().gfip_destroy(handle)
+
+
+def gfip_set_stream(handle: int, stream: int) -> int:
+    return load().gfip_set_stream(handle, stream or None)
+
+
+def gfip_workspace_size(handle, transa, transb, m, n, k, elem_bytes) -> int:
+    return load().gfip_workspace_size(handle, _b(transa), _b(transb), m, n, k, elem_bytes)
+
+
+def gfip_set_workspace(handle: int, ptr: int, nbytes: int) -> int:
+    return load().gfip_set_workspace(handle, ptr or None, nbytes)
+
+
+def gfip_set_pack_policy(handle: int, policy: int) -> int:
+    return load().gfip_set_pack_policy(handle, policy)
+
+
+def _gemm_call(name, handle, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc):
+    fn = getattr(load(), name)
+    return fn(handle, _b(transa), _b(transb), m, n, k, alpha, A or None, lda, B or None, ldb,
+              beta, C or None, ldc)
+
+
+def gfip_dgemm(*a):
+    return _gemm_call("gfip_dgemm", *a)
+
+
+def gfip_sgemm(*a):
+    return _gemm_call("gfip_sgemm", *a)
+
+
+def gfip_dgemm_direct(*a):
+    return _gemm_call("gfip_dgemm_direct", *a)
+
+
+def gfip_sgemm_direct(*a):
+    return _gemm_call("gfip_sgemm_direct", *a)
+
+
+def gfip_dgemm_pack_then_compute(*a):
+    return _gemm_call("gfip_dgemm_pack_then_compute", *a)
+
+
+def gfip_sgemm_pack_then_compute(*a):
+    return _gemm_call("gfip_sgemm_pack_then_compute", *a)
+
+
+def gfip_get_status(handle: int) -> int:
+    v = ctypes.c_uint32(0)
+    rc = load().gfip_get_status(handle, ctypes.byref(v))
+    if rc != GFIP_OK:
+        raise GemmError(rc, "gfip_get_status")
+    return int(v.value)
+
+
+def gfip_last_launch_info(handle: int) -> tuple[int, int]:
+    a, b = _int(0), _int(0)
+    load().gfip_last_launch_info(handle, ctypes.byref(a), ctypes.byref(b))
+    return int(a.value), int(b.value)
+
+
+ENTRY = {
+    ("fused", 8): "gfip_dgemm", ("fused", 4): "gfip_sgemm",
+    ("direct", 8): "gfip_dgemm_direct", ("direct", 4): "gfip_sgemm_direct",
+    ("pack_then_compute", 8): "gfip_dgemm_pack_then_compute",
+    ("pack_then_compute", 4): "gfip_sgemm_pack_then_compute",
+}
+
+
+# ---- PyTorch conveniences -------------------------------------------------------------
+
+class Handle:
+    """A library handle bound to the current CUDA device, with a torch-allocated workspace
+    that grows on demand (the library itself never allocates)."""
+
+    def __init__(self, workspace_bytes: int = 0):
+        import torch
+        self._torch = torch
+        self.h = gfip_create()
+        self.workspace = None
+        self.stream = None
+        if workspace_bytes:
+            self._set_ws(workspace_bytes)
+
+    def _set_ws(self, nbytes: int):
+        torch = self._torch
+        self.workspace = torch.empty(max(nbytes, 16), dtype=torch.uint8, device="cuda")
+        rc = gfip_set_workspace(self.h, self.workspace.data_ptr(), self.workspace.numel())
+        if rc != GFIP_OK:
+            raise GemmError(rc, "gfip_set_workspace")
+
+    def ensure_workspace(self, transa, transb, m, n, k, elem_bytes):
+        need = gfip_workspace_size(self.h, transa, transb, m, n, k, elem_bytes)
+        if self.workspace is None or self.workspace.numel() < need:
+            if self.workspace is not None:
+                self._torch.cuda.current_stream().synchronize()
+            self._set_ws(int(need * 1.25) + (1 << 20))
+
+    def bind_stream(self, stream=None):
+        torch = self._torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        if self.stream != s.cuda_stream:
+            rc = gfip_set_stream(self.h, s.cuda_stream)
+            if rc != GFIP_OK:
+                raise GemmError(rc, "gfip_set_stream")
+            self.stream = s.cuda_stream
+
+    def set_pack_policy(self, policy: int):
+        rc = gfip_set_pack_policy(self.h, policy)
+        if rc != GFIP_OK:
+            raise GemmError(rc, "gfip_set_pack_policy")
+
+    def status(self) -> int:
+        return gfip_get_status(self.h)
+
+    def close(self):
+        if self.h:
+            gfip_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default: dict = {}
+
+
+def default_handle() -> Handle:
+    import torch
+    dev = torch.cuda.current_device()
+    if dev not in _default:
+        _default[dev] = Handle()
+    return _default[dev]
+
+
+def _colmajor_ld(X, name):
+    if X.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D column-major view")
+    rows, cols = X.shape
+    if rows > 1 and X.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1); pass X.t() of a "
+                         "row-major tensor, or X.t().contiguous().t()")
+    ld = X.stride(1) if cols > 1 else max(rows, 1)
+    return max(ld, rows, 1)
+
+
+def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, transa: str = "N",
+         transb: str = "N", variant: str = "fused", handle: Handle | None = None):
+    """``C := alpha*op(A)*op(B) + beta*C`` on column-major 2-D tensors (float64 or float32).
+
+    A and B are the STORED matrices (A is m x k for transa 'N', k x m for 'T'); C is m x n
+    and updated in place (allocated when None, then beta must be 0).  CUDA tensors run
+    asynchronously on torch's current stream.  CPU tensors are copied to the GPU, computed,
+    and the result copied back into C (the end-to-end path); pinned memory makes the copies
+    asynchronous.  Returns C."""
+    import torch
+    host = not A.is_cuda
+    if host:
+        # end-to-end path: host operands in, host result out
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def to_dev(X):
+            Xd = X.to(dev, non_blocking=True)
+            if Xd.dim() == 2 and Xd.shape[0] > 1 and Xd.stride(0) != 1:
+                Xd = Xd.t().contiguous().t()
+            return Xd
+        C_d = None if C is None else to_dev(C)
+        out = gemm(to_dev(A), to_dev(B), C_d, alpha, beta, transa, transb, variant, handle)
+        if C is None:
+            C = torch.empty((out.shape[1], out.shape[0]), dtype=out.dtype,
+                            pin_memory=True).t()
+        C.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return C
+    dtype = A.dtype
+    if dtype not in (torch.float64, torch.float32) or B.dtype != dtype:
+        raise TypeError("A and B must both be float64 or both float32")
+    esz = 8 if dtype == torch.float64 else 4
+    ta, tb = transa.upper(), transb.upper()
+    m = A.shape[0] if ta == "N" else A.shape[1]
+    k = A.shape[1] if ta == "N" else A.shape[0]
+    n = B.shape[1] if tb == "N" else B.shape[0]
+    kb = B.shape[0] if tb == "N" else B.shape[1]
+    if kb != k:
+        raise ValueError(f"inner dimensions differ: op(A) is {m}x{k}, op(B) is {kb}x{n}")
+    if C is None:
+        if beta != 0.0:
+            raise ValueError("C is required when beta != 0")
+        C = torch.empty((n, m), dtype=dtype, device=A.device).t()
+    if C.dtype != dtype or tuple(C.shape) != (m, n):
+        raise ValueError(f"C must be {m}x{n} {dtype}")
+    lda, ldb, ldc = _colmajor_ld(A, "A"), _colmajor_ld(B, "B"), _colmajor_ld(C, "C")
+    h = handle or default_handle()
+    h.bind_stream()
+    h.ensure_workspace(ta, tb, m, n, k, esz)
+    name = ENTRY[(variant, esz)]
+    rc = _gemm_call(name, h.h, ta, tb, m, n, k, alpha, A.data_ptr(), lda, B.data_ptr(), ldb,
+                    beta, C.data_ptr(), ldc)
+    if rc != GFIP_OK:
+        raise GemmError(rc, name)
+    return C
