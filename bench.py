@@ -1,0 +1,437 @@
+"""Benchmark of the fused-in-packing GEMM on GB300.
+
+One step = one C := alpha*op(A)*op(B) + beta*C call of the fused FP64 routine on the
+headline workload (m = n = k = 8192, transa = transb = 'N', lda = ldb = ldc = 8199 -- not
+16-byte aligned -- alpha = 1, beta = 0.5, entries uniform[-1, 1]).  The three operands
+(1.6 GB) are larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line: GFLOP/s over the timed steps (device time, CUDA events), the roofline
+of the dominant kernel against the FP64 DFMA rate, the end-to-end figure through the public
+API with host buffers, the oracle timed on the host cores on a bounded sample, the SM clocks
+seen during the timed region, and a compact fused-vs-plain size spectrum.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-spectrum]
+
+With N > 1 (launched by torchrun) every rank runs an independent replica of the workload
+(GEMM is not sharded here); the value is the total over ranks divided by the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M = N = K = 8192     # headline size; --size overrides it (profiling of smaller cases)
+PAD = 7
+ALPHA, BETA = 1.0, 0.5
+SMS = 152
+DFMA_FLOP_PER_CLK_PER_SM = 4      # 2 DFMA lanes per clock per SM (measured by peak_probe)
+FFMA_FLOP_PER_CLK_PER_SM = 256    # 128 FFMA lanes per clock per SM
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_GFLOPS = SMS * DFMA_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ / 1e3   # 1258.6
+FP32_PEAK_GFLOPS = SMS * FFMA_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ / 1e3   # 80547.8
+HBM_GBS = 6785.2
+WORKLOAD = ("fp64 gemm m=n=k=8192 N/N lda=ldb=ldc=8199 alpha=1 beta=0.5 uniform[-1,1] "
+            "fused-in-packing")
+
+# DRAM traffic of one launch of the FP64 GEMM kernel on this workload, from an ncu capture
+# of a smaller case scaled by tiles processed (see profiles/); valid only while the kernel
+# sources hash to KERNEL_HASH.
+TRAFFIC = {"bytes_per_launch": None, "kernel_hash": None}
+KERNEL_SOURCES = ["paper_2302_08417_gb300/csrc/gfip_kernels.cuh",
+                  "paper_2302_08417_gb300/csrc/gfip_internal.h"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def gflop(m=None, n=None, k=None) -> float:
+    m, n, k = (M if m is None else m), (N if n is None else n), (K if k is None else k)
+    return 2.0 * m * n * k / 1e9
+
+
+def algorithmic_bytes(s=8, beta=BETA) -> int:
+    """Read A, read B, read C (beta != 0), write C: the bytes the GEMM must move."""
+    return s * (M * K + K * N + M * N * (1 + (beta != 0.0)))
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_operands(seed: int, dtype, m=None, n=None, k=None, pad=PAD):
+    """Column-major operands on the GPU, uniform[-1, 1], leading dimension rows + pad."""
+    import torch
+    m, n, k = (M if m is None else m), (N if n is None else n), (K if k is None else k)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    ld_a, ld_b, ld_c = m + pad, k + pad, m + pad
+
+    def mat(rows, cols, ld):
+        buf = torch.rand((cols, ld), generator=g, dtype=dtype, device="cuda") * 2 - 1
+        return buf.t()[:rows, :]   # rows x cols view, stride (1, ld), over a (cols, ld) buffer
+    return mat(m, k, ld_a), mat(k, n, ld_b), mat(m, n, ld_c)
+
+
+def host_copy(X):
+    """Pinned host copy of a column-major view with the same leading dimension."""
+    import torch
+    rows, cols = X.shape
+    ld = X.stride(1)
+    buf = torch.empty((cols, ld), dtype=X.dtype, pin_memory=True)
+    buf.t()[:rows, :].copy_(X)
+    return buf.t()[:rows, :], buf
+
+
+def cpu_oracle_sample(A_host, B_host, C_host, m, k, lda, ldb, ldc, budget_s=12.0):
+    """Times the oracle on the host cores on the first columns of the same workload."""
+    import numpy as np
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.build()
+
+    def run(cols):
+        Bs = np.ascontiguousarray(B_host[: ldb * cols])
+        Cs = np.ascontiguousarray(C_host[: ldc * cols])
+        t0 = time.perf_counter()
+        rc = oracle.gemm("N", "N", m, cols, k, ALPHA, A_host, lda, Bs, ldb, BETA, Cs, ldc,
+                         nthreads=threads)
+        dt = time.perf_counter() - t0
+        assert rc == 0
+        return dt
+
+    cols = threads
+    dt = run(cols)
+    while dt < 1.0 and cols * 4 <= N:
+        cols *= 4
+        dt = run(cols)
+    target = int(min(N, max(cols, cols * budget_s / max(dt, 1e-6))))
+    target = max(threads, target // threads * threads)
+    dt = run(target)
+    return {"value": round(gflop(m, target, k) / dt, 3), "unit": "GFLOP/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"first {target} of {N} columns of C (m=k={m}, same operands), "
+                      f"{dt:.1f} s, FP64 j-p-i triple loop, OpenMP over columns"}
+
+
+def spectrum(h, g, torch, sizes=(16, 64, 256, 1024, 4096), reps=5):
+    """Fused vs direct vs pack-then-compute GFLOP/s, N/N, ld = m + 7, beta = 0.5."""
+    out = {}
+    for dtype, esz, tag in ((torch.float64, 8, "f64"), (torch.float32, 4, "f32")):
+        rows = {}
+        for n in sizes:
+            A, B, C = make_operands(n, dtype, n, n, n)
+            ld = n + PAD
+            h.ensure_workspace("N", "N", n, n, n, esz)
+            row = {}
+            for var in ("fused", "direct", "pack_then_compute"):
+                name = g.ENTRY[(var, esz)]
+
+                def call():
+                    rc = g._gemm_call(name, h.h, "N", "N", n, n, n, ALPHA, A.data_ptr(), ld,
+                                      B.data_ptr(), ld, BETA, C.data_ptr(), ld)
+                    assert rc == 0, rc
+                for _ in range(2):
+                    call()
+                torch.cuda.synchronize()
+                best = float("inf")
+                r = reps if n <= 1024 else 2
+                for _ in range(r):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    call()
+                    e1.record()
+                    e1.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+                row[var] = round(gflop(n, n, n) / (best * 1e-3), 1)
+            rows[str(n)] = row
+        out[tag] = rows
+    return out
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2302_08417_gb300 import inputs
+    oracle.build()
+    threads = os.cpu_count() or 1
+    rng = np.random.Generator(np.random.PCG64(0))
+    lda, ldb, ldc = M + PAD, K + PAD, M + PAD
+    A = inputs.colmajor(rng, M, K, lda)
+    cols = 2 * threads
+    B = inputs.colmajor(rng, K, cols, ldb)
+    C = inputs.colmajor(rng, M, cols, ldc)
+
+    def step():
+        Cs = C.copy()
+        rc = oracle.gemm("N", "N", M, cols, K, ALPHA, A, lda, B, ldb, BETA, Cs, ldc,
+                         nthreads=threads)
+        assert rc == 0
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    val = gflop(M, cols, K) / dt
+    sample = (f"each step: the first {cols} of {N} columns of C (m=k={M}, lda=ldb=ldc={M+PAD},"
+              f" alpha=1, beta=0.5), FP64 j-p-i triple loop, OpenMP over columns")
+    print(json.dumps({
+        "impl": "reference", "metric": "fp64 gemm throughput", "value": round(val, 3),
+        "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K},
+        "cpu_baseline": {"value": round(val, 3), "unit": "GFLOP/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(val, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    global M, N, K, WORKLOAD
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-spectrum", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--size", type=int, default=M, help="m = n = k (default: the headline)")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--variant", default="fused", choices=["fused", "direct",
+                                                          "pack_then_compute"])
+    args = ap.parse_args()
+    if args.size != M or args.dtype != "f64" or args.variant != "fused":
+        M = N = K = args.size
+        WORKLOAD = (f"{args.dtype} gemm m=n=k={M} N/N lda=ldb=ldc={M + PAD} alpha=1 beta=0.5 "
+                    f"uniform[-1,1] {args.variant}")
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    from paper_2302_08417_gb300 import gemmfip as g
+
+    torch.cuda.set_device(local)
+    h = g.Handle()
+    h.bind_stream()
+    stream = torch.cuda.current_stream()
+    f64 = args.dtype == "f64"
+    esz = 8 if f64 else 4
+    A, B, C = make_operands(1234 + rank, torch.float64 if f64 else torch.float32)
+    lda, ldb, ldc = A.stride(1), B.stride(1), C.stride(1)
+    h.ensure_workspace("N", "N", M, N, K, esz)
+    entry = g.ENTRY[(args.variant, esz)]
+
+    def step():
+        rc = g._gemm_call(entry, h.h, "N", "N", M, N, K, ALPHA, A.data_ptr(), lda,
+                          B.data_ptr(), ldb, BETA, C.data_ptr(), ldc)
+        if rc != 0:
+            raise g.GemmError(rc, entry)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step, grid = g.gfip_last_launch_info(h.h)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    barrier(world)
+    torch.cuda.synchronize()
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for e0, e1 in events:
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    per_launch_ms = [e0.elapsed_time(e1) for e0, e1 in events]
+    total_ms = max_over_ranks(world, total_ms)
+    status = h.status()
+
+    value = world * args.steps * gflop() / (total_ms * 1e-3)
+    avg_launch_s = sum(per_launch_ms) / len(per_launch_ms) * 1e-3
+    achieved = gflop() / avg_launch_s
+    th = kernel_hash()
+    headline = (M == 8192 and f64 and args.variant == "fused")
+    traffic = (TRAFFIC["bytes_per_launch"]
+               if headline and TRAFFIC["kernel_hash"] == th else None)
+    peak = FP64_PEAK_GFLOPS if f64 else FP32_PEAK_GFLOPS
+
+    result = {
+        "metric": f"{args.dtype} gemm throughput ({args.variant})", "value": round(value, 2),
+        "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K, "transa": "N", "transb": "N",
+                   "lda": lda, "ldb": ldb, "ldc": ldc, "alpha": ALPHA, "beta": BETA,
+                   "l2": f"inputs larger than L2 ({3 * A.stride(1) * A.shape[1] * esz / 1e9:.2f}"
+                         " GB of operands vs 0.136 GB L2), no flush",
+                   "parallelism": f"replicas x{world}", "grid": grid},
+        "roofline": {"bound": "alu", "achieved": round(achieved, 2),
+                     "peak": round(peak, 1), "unit": "GFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": f"gfip::gemm_kernel<{'double' if f64 else 'float'}>",
+                     "peak_basis": ("152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA rate "
+                                    "measured by peak_probe)" if f64 else
+                                    "152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"),
+                     "hbm_floor_ms": round(algorithmic_bytes(s=esz) / HBM_GBS / 1e6, 3)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "device_status": status,
+    }
+
+    if rank == 0 and not args.no_cpu:
+        # end to end through the public API with pinned host buffers
+        hA, bufA = host_copy(A)
+        hB, bufB = host_copy(B)
+        hC, bufC = host_copy(C)
+        from paper_2302_08417_gb300 import gemm as pub_gemm
+        pub_gemm(hA, hB, hC, ALPHA, BETA, variant=args.variant, handle=h)   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            pub_gemm(hA, hB, hC, ALPHA, BETA, variant=args.variant, handle=h)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        result["e2e"] = {"value": round(gflop() / e2e_s, 2), "unit": "GFLOP/s",
+                         "h2d_bytes_per_step": g.span_bytes(hA) + g.span_bytes(hB)
+                         + g.span_bytes(hC),
+                         "d2h_bytes_per_step": g.span_bytes(hC),
+                         "steps": args.e2e_steps,
+                         "path": "paper_2302_08417_gb300.gemm(pinned host tensors) -> "
+                                 f"{entry}; copies and compute inside the timed region"}
+        # oracle on the host cores, bounded sample of the same workload
+        result["cpu_baseline"] = cpu_oracle_sample(
+            bufA.numpy().reshape(-1), bufB.numpy().reshape(-1), bufC.numpy().reshape(-1),
+            M, K, lda, ldb, ldc)
+    if rank == 0 and not args.no_spectrum:
+        result["spectrum_gflops"] = spectrum(h, g, torch)
+        result["spectrum_gflops"]["note"] = ("N/N, ld = m + 7, beta = 0.5, best of a few "
+                                             "launches, CUDA events")
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

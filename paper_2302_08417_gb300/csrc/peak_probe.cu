@@ -18,7 +18,7 @@
         }                                                                              \
     } while (0)
 
-constexpr int CHAINS = 8;
+constexpr int CHAINS = 16;
 
 __global__ void dfma_kernel(double *out, int iters, double a, double b)
 {

@@ -251,6 +251,29 @@ def _colmajor_ld(X, name):
     return max(ld, rows, 1)
 
 
+def _span(X):
+    """1-D view of the storage a column-major 2-D view X occupies."""
+    import torch
+    rows, cols = X.shape
+    ld = _colmajor_ld(X, "matrix")
+    n = ld * (cols - 1) + rows if rows and cols else 0
+    return torch.as_strided(X, (n,), (1,))
+
+
+def span_bytes(X) -> int:
+    return _span(X).numel() * X.element_size()
+
+
+def _span_to_device(X):
+    import torch
+    rows, cols = X.shape
+    ld = _colmajor_ld(X, "matrix")
+    flat = _span(X).to(torch.device("cuda", torch.cuda.current_device()), non_blocking=True)
+    if flat.numel() == 0:
+        return torch.empty((rows, cols), dtype=X.dtype, device=flat.device)
+    return torch.as_strided(flat, (rows, cols), (1, ld))
+
+
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, transa: str = "N",
          transb: str = "N", variant: str = "fused", handle: Handle | None = None):
     """``C := alpha*op(A)*op(B) + beta*C`` on column-major 2-D tensors (float64 or float32).
@@ -263,22 +286,18 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, transa: str = "N",
     import torch
     host = not A.is_cuda
     if host:
-        # end-to-end path: host operands in, host result out
-        dev = torch.device("cuda", torch.cuda.current_device())
-
-        def to_dev(X):
-            Xd = X.to(dev, non_blocking=True)
-            if Xd.dim() == 2 and Xd.shape[0] > 1 and Xd.stride(0) != 1:
-                Xd = Xd.t().contiguous().t()
-            return Xd
-        C_d = None if C is None else to_dev(C)
-        out = gemm(to_dev(A), to_dev(B), C_d, alpha, beta, transa, transb, variant, handle)
-        if C is None:
-            C = torch.empty((out.shape[1], out.shape[0]), dtype=out.dtype,
-                            pin_memory=True).t()
-        C.copy_(out, non_blocking=True)
+        # end-to-end path: host operands in, host result out; each operand's storage span
+        # (ld*(cols-1) + rows elements) is copied as is, so leading dimensions are kept
+        C_h = C
+        if C_h is None:
+            m_ = A.shape[0] if transa.upper() == "N" else A.shape[1]
+            n_ = B.shape[1] if transb.upper() == "N" else B.shape[0]
+            C_h = torch.empty((n_, m_), dtype=A.dtype, pin_memory=True).t()
+        dA, dB, dC = (_span_to_device(X) for X in (A, B, C_h))
+        gemm(dA, dB, dC, alpha, beta, transa, transb, variant, handle)
+        _span(C_h).copy_(_span(dC), non_blocking=True)
         torch.cuda.current_stream().synchronize()
-        return C
+        return C_h
     dtype = A.dtype
     if dtype not in (torch.float64, torch.float32) or B.dtype != dtype:
         raise TypeError("A and B must both be float64 or both float32")
