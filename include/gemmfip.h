@@ -57,6 +57,8 @@ typedef struct gfip_handle_s *gfip_handle_t;
 #define GFIP_ERR_DEVICE 5       /* the current device is not an sm_103 GPU                 */
 #define GFIP_ERR_SIZE 6         /* a dimension or leading dimension exceeds 2^31 - 1       */
 #define GFIP_ERR_ARG 7          /* an invalid value for a non-BLAS argument                */
+#define GFIP_ERR_SCRATCH_LIMIT 8 /* gfip_dgemm_noalloc: the problem needs more scratch than
+                                    GFIP_NOALLOC_SCRATCH_BYTES                               */
 
 /* Device status bits, reported by gfip_get_status(). */
 #define GFIP_STATUS_BAD_SEGMENT 0x1u   /* a split tile saw more partial sums than planned */
@@ -138,6 +140,35 @@ int gfip_last_launch_info(gfip_handle_t handle, int *launches, int *grid);
 
 /* Static description of a return code. */
 const char *gfip_error_string(int code);
+
+/* ---- Allocation-free entry point ----------------------------------------------------------
+ * The paper has no counterpart to this routine; it exists for callers that cannot allocate
+ * device memory or hand the library a workspace: code behind the plain BLAS dgemm interface
+ * (which has no workspace argument), applications that own every byte of device memory
+ * through their own pool, and code running where cudaMalloc is not allowed.
+ *
+ * gfip_dgemm_noalloc computes exactly what gfip_dgemm computes (the fused-in-packing FP64
+ * GEMM, same kernel, same result bits), with the reference-BLAS argument list plus a stream
+ * (a cudaStream_t passed as void*; NULL = legacy default stream).  It takes no handle and
+ * allocates nothing: its scratch memory (packed panels, ready words, split-tile partial sums)
+ * is one statically sized device array of GFIP_NOALLOC_SCRATCH_BYTES bytes inside this
+ * library, which every GPU that loads the library holds until the process exits.
+ *
+ * A problem whose scratch would exceed that size is rejected with GFIP_ERR_SCRATCH_LIMIT
+ * before anything is launched (square FP64 problems up to about m = n = k = 1600 fit; any
+ * size fits the handle-based routines).  The first call on a device sets the array up: it
+ * looks up the array's device address and clears its control words with an asynchronous
+ * memset on the given stream, so make that first call before any stream capture.
+ *
+ * All calls on a device share the one array, and it keeps the last call's contents (each call
+ * tags its control words, so stale contents are never mistaken for its own).  Calls that can
+ * overlap on the GPU -- on different streams, or from several host threads without ordering
+ * -- race on the array and give wrong results; order them on one stream. */
+#define GFIP_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+int gfip_dgemm_noalloc(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                       const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                       double *C, int64_t ldc, void *stream);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <new>
 
 #include <cuda_runtime.h>
@@ -502,8 +503,80 @@ const char *gfip_error_string(int code)
     case GFIP_ERR_DEVICE: return "device is not sm_103";
     case GFIP_ERR_SIZE: return "dimension exceeds 2^31-1";
     case GFIP_ERR_ARG: return "invalid argument value";
+    case GFIP_ERR_SCRATCH_LIMIT:
+        return "problem needs more scratch than the allocation-free routine's static array";
     default: return "unknown error";
     }
 }
 
 }  // extern "C"
+
+// ---- Allocation-free entry point ---------------------------------------------------------
+// Scratch of gfip_dgemm_noalloc: one static device array per GPU that loads this library.
+// In host code `g_noalloc_scratch` is only a stand-in symbol, never a device address; the
+// address comes from cudaGetSymbolAddress at set-up.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GFIP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocDevice {
+    std::mutex mu;          // serialises host-side use of this device's state
+    bool ready = false;
+    Handle h;               // static-storage handle whose workspace is the static array
+};
+
+NoAllocDevice g_noalloc[kNoAllocMaxDevices];
+
+// Set-up for the current device, once: check the device, look up the array's device address
+// with that device current, and point the device's static handle at it.  The handle's
+// control-word region starts empty, so the first call clears it on its stream.
+int noalloc_setup(NoAllocDevice &d, int dev)
+{
+    if (d.ready) return GFIP_OK;
+    int major = 0, minor = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GFIP_ERR_CUDA;
+    if (!(major == 10 && minor == 3)) return GFIP_ERR_DEVICE;
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr)
+        return GFIP_ERR_CUDA;
+    d.h.device = dev;
+    d.h.sms = sms;
+    d.h.ws = reinterpret_cast<unsigned char *>(ptr);
+    d.h.ws_bytes = GFIP_NOALLOC_SCRATCH_BYTES;
+    d.h.ctrl_bytes = 0;
+    d.h.epoch = 0;
+    d.h.pack_policy = GFIP_PACK_AUTO;
+    d.ready = true;
+    return GFIP_OK;
+}
+
+}  // namespace
+
+extern "C" int gfip_dgemm_noalloc(char transa, char transb, int64_t m, int64_t n, int64_t k,
+                                  double alpha, const double *A, int64_t lda, const double *B,
+                                  int64_t ldb, double beta, double *C, int64_t ldc, void *stream)
+{
+    const int info = check_args(transa, transb, m, n, k, lda, ldb, ldc);
+    if (info != 0) return info;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GFIP_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GFIP_ERR_DEVICE;
+    NoAllocDevice &d = g_noalloc[dev];
+    std::lock_guard<std::mutex> lock(d.mu);
+    const int rc = noalloc_setup(d, dev);
+    if (rc != GFIP_OK) return rc;
+    d.h.stream = reinterpret_cast<cudaStream_t>(stream);
+    // Reject, before launching anything, a problem whose scratch does not fit the array.
+    const bool use_ab = !(alpha == 0.0 || k == 0);
+    if (m > 0 && n > 0 && use_ab && !too_big(m) && !too_big(n) && !too_big(k)) {
+        const Plan<double> pl = make_plan<double>(&d.h, Variant::Fused, (int)m, (int)n, (int)k);
+        if (total_bytes(&d.h, pl) > d.h.ws_bytes) return GFIP_ERR_SCRATCH_LIMIT;
+    }
+    return gemm_entry<double>(reinterpret_cast<gfip_handle_t>(&d.h), Variant::Fused, transa,
+                              transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}

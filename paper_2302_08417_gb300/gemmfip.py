@@ -26,6 +26,8 @@ GFIP_ERR_NULLPTR = 4
 GFIP_ERR_DEVICE = 5
 GFIP_ERR_SIZE = 6
 GFIP_ERR_ARG = 7
+GFIP_ERR_SCRATCH_LIMIT = 8
+GFIP_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 GFIP_STATUS_BAD_SEGMENT = 0x1
 
 GFIP_PACK_AUTO, GFIP_PACK_NONE, GFIP_PACK_A, GFIP_PACK_B, GFIP_PACK_BOTH = range(5)
@@ -51,6 +53,8 @@ SIGNATURES = {
     "gfip_get_status": (_int, [_ptr, ctypes.POINTER(ctypes.c_uint32)]),
     "gfip_last_launch_info": (_int, [_ptr, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "gfip_error_string": (ctypes.c_char_p, [_int]),
+    "gfip_dgemm_noalloc": (_int, [_chr, _chr, _i64, _i64, _i64, _dbl, _ptr, _i64, _ptr, _i64,
+                                  _dbl, _ptr, _i64, _ptr]),
 }
 
 _lock = threading.Lock()
@@ -161,6 +165,14 @@ def gfip_last_launch_info(handle: int) -> tuple[int, int]:
     a, b = _int(0), _int(0)
     load().gfip_last_launch_info(handle, ctypes.byref(a), ctypes.byref(b))
     return int(a.value), int(b.value)
+
+
+def gfip_dgemm_noalloc(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                       stream=0) -> int:
+    """The allocation-free FP64 entry point: BLAS dgemm arguments plus a stream, no handle and
+    no workspace; its scratch is a fixed static device array inside the library."""
+    return load().gfip_dgemm_noalloc(_b(transa), _b(transb), m, n, k, alpha, A or None, lda,
+                                     B or None, ldb, beta, C or None, ldc, stream or None)
 
 
 ENTRY = {
