@@ -165,9 +165,9 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
     pl.off_count = off;
     off += round_up((size_t)pl.tiles * 8, kAlign);
     pl.off_state_a = off;
-    if (pl.mode_a == gfip::MODE_FIP) off += round_up((size_t)pl.mt * pl.kt * 8, kAlign);
+    if (pl.mode_a == gfip::MODE_FIP) off += round_up((size_t)pl.mt * (pl.kt + 1) * 8, kAlign);
     pl.off_state_b = off;
-    if (pl.mode_b == gfip::MODE_FIP) off += round_up((size_t)pl.nt * pl.kt * 8, kAlign);
+    if (pl.mode_b == gfip::MODE_FIP) off += round_up((size_t)pl.nt * (pl.kt + 1) * 8, kAlign);
     pl.ctrl_needed = off;
 
     // Data region (relative to its start): partial sums, packed A, packed B.

@@ -22,8 +22,18 @@ template <typename T> struct TileCfg;
 template <> struct TileCfg<double> {
     static constexpr int BM = 64, BN = 64, BK = 16, THREADS = 256, STAGES = 4, MIN_BLOCKS = 2;
 };
+#ifndef GFIP_F32_MIN_BLOCKS
+#define GFIP_F32_MIN_BLOCKS 2
+#endif
+#ifndef GFIP_F32_STAGES
+#define GFIP_F32_STAGES 3
+#endif
+#ifndef GFIP_F32_BK
+#define GFIP_F32_BK 32
+#endif
 template <> struct TileCfg<float> {
-    static constexpr int BM = 128, BN = 128, BK = 16, THREADS = 256, STAGES = 3, MIN_BLOCKS = 1;
+    static constexpr int BM = 128, BN = 128, BK = GFIP_F32_BK, THREADS = 256;
+    static constexpr int STAGES = GFIP_F32_STAGES, MIN_BLOCKS = GFIP_F32_MIN_BLOCKS;
 };
 
 // Everything one launch of the GEMM kernel needs.  Plain data, passed by value.
@@ -42,8 +52,9 @@ template <typename T> struct GemmParams {
     int dp_tiles;     // tiles [0, dp_tiles) are data-parallel: tile t runs on CTA t % grid
     int64_t sk_iters; // (tiles - dp_tiles) * kt iterations split evenly over the CTAs
     int mode_a, mode_b;
-    unsigned long long *state_a;     // [mt * kt] epoch-tagged ready words of packed A
-    unsigned long long *state_b;     // [nt * kt] same for B
+    unsigned long long *state_a;     // [mt * kt] epoch-tagged ready words of packed A tiles,
+                                     // then [mt] words "whole panel published"
+    unsigned long long *state_b;     // [nt * kt + nt] same for B
     unsigned long long *tile_count;  // [tiles] epoch-tagged arrival counters of split tiles
     T *pack_a;                       // [mt * kt] tiles of BM * BK elements
     T *pack_b;                       // [nt * kt] tiles of BN * BK elements

@@ -10,22 +10,24 @@
 //    contiguous 16-byte copies and no address arithmetic, and fringes are zero-padded once,
 //    when packing (Sec. 2.2).
 //
-//  * Fused-in packing (Sec. 3.1 Alg. 1, Sec. 3.2).  In MODE_FIP the first CTA that needs a
-//    (panel, k-block) claims it with one atomic, reads the raw strided operand, computes with
-//    it, and in the same pass writes the tile image to the packed buffer, then publishes it.
-//    Every later CTA that needs it loads the packed copy.  A CTA that finds the tile claimed
-//    but not yet published reads the raw operand itself and never waits, so there is no
-//    inter-CTA wait anywhere in the kernel (Sec. 3.5: each packer packs its own share and
-//    only consumers that come later use the packed data).
+//  * Fused-in packing (Sec. 3.1 Alg. 1, Sec. 3.2).  Tiles are ordered producers first: the
+//    tiles of the first tile column come first and pack the A panels, then the rest of the
+//    first tile row, which pack the B panels.  A producer reads its raw strided operand
+//    k-block by k-block, computes with it, and in the same pass writes the staged tile image
+//    to the packed buffer and publishes it (an epoch-tagged ready word, release order).  Every
+//    other tile looks the ready word up (acquire load) a few k-blocks ahead: published tiles
+//    are read packed, the rest raw.  Nothing ever waits for another CTA (Sec. 3.5: packers
+//    pack their own share; only consumers that come later use the packed data).
 //
-//  * One code path for all sizes.  Tiles are scheduled as data-parallel waves over the
-//    persistent CTAs; the tiles of the last, partial wave (plus one full wave) are split
-//    evenly along k over all CTAs ("stream-K"), and split tiles are summed in a fixed order
-//    by whichever CTA finishes last.  The split points depend only on the problem shape and
-//    the grid, so every variant (fused, direct, pack-then-compute) and every pack policy
-//    produces identical bits: packing changes where a tile is read from, never its value.
+//  * One code path for all sizes.  Tiles run as data-parallel waves over the persistent
+//    CTAs; the tiles of the last, partial wave (plus one full wave) are split evenly along k
+//    over all CTAs ("stream-K"), and split tiles are summed in a fixed order by whichever CTA
+//    finishes last.  The split points depend only on the problem shape and the grid, so every
+//    variant (fused, direct, pack-then-compute) and every pack policy produces identical
+//    bits: packing changes where a tile is read from, never its value.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 
 #include "gfip_internal.h"
@@ -41,7 +43,8 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Element copy global -> shared through L1, zero-filling the destination when !ok.
+// Element copy global -> shared through L1, zero-filling the destination when !ok (no
+// bytes are read from src then).
 template <int BYTES>
 __device__ __forceinline__ void cp_async_elem(uint32_t dst, const void *src, bool ok)
 {
@@ -67,125 +70,200 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Offset (in elements) of element (x, kk) inside a BX x BK operand tile.  x runs along m
-// (for A) or n (for B), kk along k.  Rows of W = 128/sizeof(T) consecutive x form one
-// 128-byte segment per kk; the 16-byte chunks of a segment are XOR-permuted by (kk mod 8).
-template <typename T, int BK> __device__ __forceinline__ int tile_off(int x, int kk)
-{
-    constexpr int W = 128 / static_cast<int>(sizeof(T));
-    constexpr int CH = 16 / static_cast<int>(sizeof(T));
-    return (x / W) * (BK * W) + kk * W + ((x % W) ^ ((kk & 7) * CH));
-}
+// Layout of one BX x BK operand tile (x runs along m for A, along n for B; kk along k).
+// The tile is cut into BX/W segments of W = 128/sizeof(T) consecutive x; a segment holds BK
+// rows (one per kk) of W elements, i.e. 128 bytes.
+//  * Packed copy in global memory: the rows back to back, row r = (x / W) * BK + kk
+//    (ROWS rows, no padding), so a packed tile is one contiguous block of 16-byte chunks.
+//  * Shared memory: the same rows with a pitch of P = W + PADE elements.  The padding moves
+//    consecutive rows across banks, so the raw loads that write 8 consecutive kk of 4
+//    consecutive x in one warp instruction are bank-conflict free, and a compute-loop
+//    fragment is the address base + kk * P (an immediate offset).
+template <typename T, int BX, int BK> struct TileLayout {
+    static constexpr int W = 128 / static_cast<int>(sizeof(T));
+    static constexpr int PADE = 4;                // 4 floats (16 B) or 4 doubles (32 B)
+    static constexpr int P = W + PADE;            // shared-memory row pitch, elements
+    static constexpr int SEG = BK * P;            // shared-memory segment pitch, elements
+    static constexpr int ELEMS = (BX / W) * SEG;  // shared-memory elements per tile
+    static constexpr int ROWS = (BX / W) * BK;    // 128-byte rows per tile
+    static constexpr int PACKED = BX * BK;        // packed elements per tile
+    static_assert(BX % W == 0, "tile must be whole 128-byte segments");
+    static_assert((P * sizeof(T)) % 16 == 0, "rows must stay 16-byte aligned");
+    static __device__ __forceinline__ int off(int x, int kk)
+    {
+        return (x / W) * SEG + kk * P + (x % W);
+    }
+};
 
-// Raw strided tile load: element (x, kk) of the BX x BK tile at (x0, k0) of op(X), X = A
-// (x = row of op(A)) or B (x = column of op(B)), into shared memory at sdst.  Positions
-// outside the X_ext x K_ext operand are zero-filled.  contig_x: element at g[x + kk*ld],
-// else at g[kk + x*ld].  Either way consecutive lanes read consecutive addresses, and the
-// swizzle keeps the shared-memory writes free of bank conflicts.
-template <typename T, int BX, int BK, int THREADS>
-__device__ __forceinline__ void load_raw_tile(uint32_t sdst, const T *__restrict__ g, int64_t ld,
-                                              int x0, int k0, int x_ext, int k_ext, int contig_x,
-                                              int tid)
-{
-    constexpr int PER = BX * BK / THREADS;
+// Raw strided loads of one operand's BX x BK tiles, k-block after k-block.  Element (x, kk)
+// of the tile at (x0, k0) of op(X) sits at g[(x0+x) + (k0+kk)*ld] when CONTIG (x runs along
+// memory) and at g[(k0+kk) + (x0+x)*ld] otherwise.  Each thread owns PER fixed elements of
+// the tile; their addresses differ from one base pointer by per-element constants, so a
+// k-block costs one pointer increment plus one copy per element.  Out-of-range elements are
+// zero-filled (the fringe padding of Sec. 2.2).
+//   CONTIG: x = tid % BX, kk = tid / BX + r * (THREADS / BX): a warp reads 32 consecutive x.
+//   else:   a warp covers 4 consecutive x by 8 consecutive k; x = 4*warp + lane/8 + 32*(r%G),
+//           kk = lane%8 + 8*(r/G), G = BX/32: four runs of 8 contiguous elements per warp.
+template <typename T, int BX, int BK, int THREADS, bool CONTIG> struct RawLoader {
+    using L = TileLayout<T, BX, BK>;
+    static constexpr int PER = BX * BK / THREADS;
+    static constexpr int G = BX / 32;
     static_assert(PER * THREADS == BX * BK, "tile must divide over the threads");
-    if (contig_x) {
+    static_assert(!CONTIG || THREADS % BX == 0, "contiguous pattern needs THREADS % BX == 0");
+    static_assert(CONTIG || (THREADS == 256 && BK % 8 == 0 && PER == G * (BK / 8)),
+                  "transposed pattern assumes 8 warps");
+
+    const T *g;       // operand base (a valid address for zero-filled copies)
+    const T *p;       // this thread's element 0 at the next k-block to issue
+    int64_t ld;
+    uint32_t xok;     // bit r (CONTIG: bit 0): x of element r lies inside the operand
+    int kk0;          // kk of element 0
+    uint32_t s0;      // shared-memory byte offset (within a stage) of element 0
+
+    __device__ __forceinline__ void init(const T *g_, int64_t ld_, int x0, int k0, int x_ext,
+                                         int tid)
+    {
+        g = g_;
+        ld = ld_;
+        if (CONTIG) {
+            const int x = tid % BX;
+            kk0 = tid / BX;
+            p = g + (int64_t)(x0 + x) + (int64_t)(k0 + kk0) * ld;
+            xok = (x0 + x < x_ext) ? 1u : 0u;
+            s0 = 0;
+        } else {
+            const int lane = tid & 31, w = tid >> 5;
+            const int x = 4 * w + (lane >> 3);
+            kk0 = lane & 7;
+            p = g + (int64_t)(k0 + kk0) + (int64_t)(x0 + x) * ld;
+            xok = 0;
 #pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int e = tid + r * THREADS;
-            const int x = e % BX, kk = e / BX;
-            const int gx = x0 + x, gk = k0 + kk;
-            const bool ok = (gx < x_ext) && (gk < k_ext);
-            const T *src = ok ? g + (int64_t)gx + (int64_t)gk * ld : g;
-            cp_async_elem<sizeof(T)>(sdst + tile_off<T, BK>(x, kk) * sizeof(T), src, ok);
-        }
-    } else {
-        // a warp covers 4 consecutive x by 8 consecutive k: 4 runs of 8 contiguous elements
-        const int lane = tid & 31, w = tid >> 5;
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int b = w + r * (THREADS / 32);
-            const int x = (b % (BX / 4)) * 4 + (lane >> 3);
-            const int kk = (b / (BX / 4)) * 8 + (lane & 7);
-            const int gx = x0 + x, gk = k0 + kk;
-            const bool ok = (gx < x_ext) && (gk < k_ext);
-            const T *src = ok ? g + (int64_t)gk + (int64_t)gx * ld : g;
-            cp_async_elem<sizeof(T)>(sdst + tile_off<T, BK>(x, kk) * sizeof(T), src, ok);
+            for (int r = 0; r < G; ++r)
+                if (x0 + x + 32 * r < x_ext) xok |= 1u << r;
+            s0 = L::off(x, kk0) * sizeof(T);
         }
     }
-}
 
-// Packed tile load: the packed tile is the shared-memory image, copied in 16-byte pieces.
+    // Copies the next k-block's tile (kleft = rows of k still inside the operand) into the
+    // stage at byte address sdst, then advances to the following k-block.
+    __device__ __forceinline__ void issue(uint32_t sdst, int kleft, int tid)
+    {
+        if (CONTIG) {
+            const int x = tid % BX;
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int kk = kk0 + r * (THREADS / BX);
+                const bool ok = xok && (kk < kleft);
+                const T *src = ok ? p + (int64_t)(r * (THREADS / BX)) * ld : g;
+                cp_async_elem<sizeof(T)>(sdst + L::off(x, kk) * sizeof(T), src, ok);
+            }
+            p += (int64_t)BK * ld;
+        } else {
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int gx = r % G, gk = r / G;
+                const bool ok = ((xok >> gx) & 1u) && (kk0 + 8 * gk < kleft);
+                const T *src = ok ? p + (int64_t)(32 * gx) * ld + 8 * gk : g;
+                // +32 x = +32/W segments; +8 kk = +8 rows
+                const uint32_t soff = s0 + ((32 / L::W) * gx * L::SEG + 8 * gk * L::P) * sizeof(T);
+                cp_async_elem<sizeof(T)>(sdst + soff, src, ok);
+            }
+            p += BK;
+        }
+    }
+
+    __device__ __forceinline__ void skip()
+    {
+        p += CONTIG ? (int64_t)BK * ld : (int64_t)BK;
+    }
+};
+
+// Packed tile load: 16-byte chunk c of the packed tile goes to row c/8, bytes (c%8)*16 of
+// the padded shared-memory tile.
 template <typename T, int BX, int BK, int THREADS>
 __device__ __forceinline__ void load_packed_tile(uint32_t sdst, const T *src, int tid)
 {
-    constexpr int CHUNKS = BX * BK * static_cast<int>(sizeof(T)) / 16;
+    using L = TileLayout<T, BX, BK>;
+    constexpr int CHUNKS = L::ROWS * 8;
+    constexpr int PB = L::P * static_cast<int>(sizeof(T));
     const char *s = reinterpret_cast<const char *>(src);
 #pragma unroll
-    for (int c = tid; c < CHUNKS; c += THREADS) cp_async_16(sdst + c * 16, s + c * 16);
+    for (int c = tid; c < CHUNKS; c += THREADS)
+        cp_async_16(sdst + (c >> 3) * PB + (c & 7) * 16, s + c * 16);
 }
 
-// Writes the shared-memory image of a tile to its packed slot (the fused pack store).
+// Writes a staged tile to its packed slot (the fused pack store): the inverse mapping.
 template <typename T, int BX, int BK, int THREADS>
 __device__ __forceinline__ void store_packed_tile(T *dst, const T *stile, int tid)
 {
-    constexpr int CHUNKS = BX * BK * static_cast<int>(sizeof(T)) / 16;
-    const uint4 *s = reinterpret_cast<const uint4 *>(stile);
+    using L = TileLayout<T, BX, BK>;
+    constexpr int CHUNKS = L::ROWS * 8;
+    constexpr int PB = L::P * static_cast<int>(sizeof(T));
+    const char *s = reinterpret_cast<const char *>(stile);
     uint4 *d = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
-    for (int c = tid; c < CHUNKS; c += THREADS) __stcg(d + c, s[c]);
+    for (int c = tid; c < CHUNKS; c += THREADS)
+        __stcg(d + c, *reinterpret_cast<const uint4 *>(s + (c >> 3) * PB + (c & 7) * 16));
 }
 
-// Claims or looks up one (panel, k-block) of a packed operand.  The word holds
-// (epoch << 32) | ready.  One atomic max with (epoch << 32) returns the previous value:
-// an older epoch means nobody has claimed the tile in this call, so this CTA now owns it and
-// packs it; (epoch << 32) | 0 means another CTA is packing it right now (read raw);
-// (epoch << 32) | 1 means it is published (read packed).  The fetch and the classification
-// are separate so the atomic's latency overlaps the compute of the current k-block.
-__device__ __forceinline__ unsigned long long claim_fetch(unsigned long long *word,
-                                                          unsigned int epoch)
+// Relaxed read of a ready word; pair a "published" result with fence_acquire() before the
+// packed data is read (the acquire pattern of the PTX memory model).  Split from the fence so
+// the load's latency overlaps a k-block of compute.
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *word)
 {
-    const unsigned long long tag = static_cast<unsigned long long>(epoch) << 32;
-    unsigned long long old;
-    asm volatile("atom.acquire.gpu.global.max.u64 %0, [%1], %2;\n"
-                 : "=l"(old)
-                 : "l"(word), "l"(tag)
-                 : "memory");
-    return old;
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(word) : "memory");
+    return v;
 }
 
-__device__ __forceinline__ int claim_classify(unsigned long long old, unsigned int epoch)
+__device__ __forceinline__ void fence_acquire()
 {
-    const unsigned long long tag = static_cast<unsigned long long>(epoch) << 32;
-    if (old == (tag | 1ull)) return DEC_PACKED;
-    if (old < tag) return DEC_PRODUCE;
-    return DEC_RAW;
+    asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
 }
 
-// Marks a packed tile as published.  Called by thread 0 after a CTA barrier that follows
-// every thread's pack stores of that tile.
+__device__ __forceinline__ unsigned long long ready_value(unsigned int epoch)
+{
+    return (static_cast<unsigned long long>(epoch) << 32) | 1ull;
+}
+
+// Publishes a packed tile.  Called by thread 0 after a CTA barrier that follows every
+// thread's pack stores of that tile; the fence and the release make them visible first.
 __device__ __forceinline__ void publish(unsigned long long *word, unsigned int epoch)
 {
     const unsigned long long v = (static_cast<unsigned long long>(epoch) << 32) | 1ull;
     __threadfence();
-    asm volatile("red.release.gpu.global.max.u64 [%0], %1;\n" ::"l"(word), "l"(v) : "memory");
+    asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(word), "l"(v) : "memory");
+}
+
+// Tile order, producers first: t < mt are (t, 0) (first tile column, packs A), the next
+// nt - 1 are (0, j) (rest of the first tile row, packs B), then the remaining
+// (mt-1) x (nt-1) tiles in column-major order.
+__device__ __forceinline__ void tile_coords(int t, int mt, int nt, int &i, int &j)
+{
+    if (t < mt) {
+        i = t;
+        j = 0;
+        return;
+    }
+    t -= mt;
+    if (t < nt - 1) {
+        i = 0;
+        j = t + 1;
+        return;
+    }
+    t -= nt - 1;
+    i = 1 + t % (mt - 1);
+    j = 1 + t / (mt - 1);
 }
 
 template <typename T> struct GemmSmem {
     using Cfg = TileCfg<T>;
-    T a[Cfg::STAGES][Cfg::BM * Cfg::BK];
-    T b[Cfg::STAGES][Cfg::BN * Cfg::BK];
+    T a[Cfg::STAGES][TileLayout<T, Cfg::BM, Cfg::BK>::ELEMS];
+    T b[Cfg::STAGES][TileLayout<T, Cfg::BN, Cfg::BK>::ELEMS];
     int dec_a[2 * Cfg::STAGES];
     int dec_b[2 * Cfg::STAGES];
+    int full_a, full_b;  // the tile's whole A (B) panel is already published
     int flag;
-};
-
-template <typename T> struct Vec16;
-template <> struct Vec16<double> {
-    using type = double2;
-};
-template <> struct Vec16<float> {
-    using type = float4;
 };
 
 // Loads one 16-byte chunk (CH elements) from shared memory.
@@ -205,7 +283,7 @@ template <> __device__ __forceinline__ void lds16<float>(float *dst, const float
     dst[3] = v.w;
 }
 
-template <typename T> struct Kernel {
+template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
     using Cfg = TileCfg<T>;
     static constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
     static constexpr int THREADS = Cfg::THREADS, STAGES = Cfg::STAGES;
@@ -214,66 +292,130 @@ template <typename T> struct Kernel {
     static constexpr int TX = BM / TM;               // threads along m
     static_assert(TX * (BN / TN) == THREADS, "thread grid must cover the tile");
     static constexpr int DEC = 2 * STAGES;
+    using LoadA = RawLoader<T, BM, BK, THREADS, ACONTIG>;
+    using LoadB = RawLoader<T, BN, BK, THREADS, BCONTIG>;
 
-    // Decision for one operand tile under a launch mode, in two steps (see claim_fetch).
-    static __device__ __forceinline__ unsigned long long fetch(int mode, unsigned long long *state,
-                                                               unsigned int epoch)
+    // Decision for one operand tile at one k-block, in two steps so the ready-word load
+    // overlaps compute.  FIP: the first tile column produces A panels, the first tile row
+    // produces B panels; the others read what is already published (the whole panel, known
+    // at segment start, or this k-block's word).
+    //   need_word(): does the decision need this k-block's ready word?
+    //   classify():  the decision, given that word (relaxed-loaded) when needed.
+    static __device__ __forceinline__ bool need_word(int mode, bool producer, int full)
     {
-        return mode == MODE_FIP ? claim_fetch(state, epoch) : 0ull;
+        return mode == MODE_FIP && !producer && !full;
     }
-    static __device__ __forceinline__ int classify(int mode, unsigned long long old,
-                                                   unsigned int epoch)
+    static __device__ __forceinline__ int classify(int mode, bool producer, int full,
+                                                   unsigned long long word, unsigned int epoch)
     {
         if (mode == MODE_RAW) return DEC_RAW;
         if (mode == MODE_PACKED) return DEC_PACKED;
-        return claim_classify(old, epoch);
+        if (producer) return DEC_PRODUCE;
+        if (full) return DEC_PACKED;
+        return word == ready_value(epoch) ? DEC_PACKED : DEC_RAW;
+    }
+
+    struct Words {
+        unsigned long long a, b;
+    };
+
+    static __device__ __forceinline__ Words fetch_words(const GemmParams<T> &p,
+                                                        const GemmSmem<T> &sm, int i, int j,
+                                                        int kb)
+    {
+        Words w{0ull, 0ull};
+        if (need_word(p.mode_a, j == 0, sm.full_a))
+            w.a = ld_relaxed(p.state_a + (int64_t)i * p.kt + kb);
+        if (need_word(p.mode_b, i == 0, sm.full_b))
+            w.b = ld_relaxed(p.state_b + (int64_t)j * p.kt + kb);
+        return w;
+    }
+
+    // Stores the decisions for local k-block q; returns true if one of them reads a tile
+    // published by another CTA (the caller then issues fence_acquire()).
+    static __device__ __forceinline__ bool store_decisions(const GemmParams<T> &p,
+                                                           GemmSmem<T> &sm, int i, int j,
+                                                           Words w, int q)
+    {
+        const int da = classify(p.mode_a, j == 0, sm.full_a, w.a, p.epoch);
+        const int db = classify(p.mode_b, i == 0, sm.full_b, w.b, p.epoch);
+        sm.dec_a[q % DEC] = da;
+        sm.dec_b[q % DEC] = db;
+        return (da == DEC_PACKED && p.mode_a == MODE_FIP && !sm.full_a) ||
+               (db == DEC_PACKED && p.mode_b == MODE_FIP && !sm.full_b);
     }
 
     static __device__ __forceinline__ void issue(const GemmParams<T> &p, GemmSmem<T> &sm,
-                                                 int i, int j, int kb, int q, int tid)
+                                                 LoadA &la, LoadB &lb, int i, int j, int kb,
+                                                 int q, int tid)
     {
         const int stage = q % STAGES;
-        const int da = sm.dec_a[q % DEC], db = sm.dec_b[q % DEC];
+        const int kleft = p.k - kb * BK;
         const uint32_t sa = smem_addr(sm.a[stage]), sb = smem_addr(sm.b[stage]);
-        if (da == DEC_PACKED)
+        if (sm.dec_a[q % DEC] == DEC_PACKED) {
             load_packed_tile<T, BM, BK, THREADS>(
                 sa, p.pack_a + ((int64_t)i * p.kt + kb) * (BM * BK), tid);
-        else
-            load_raw_tile<T, BM, BK, THREADS>(sa, p.A, p.lda, i * BM, kb * BK, p.m, p.k,
-                                              p.a_contig_m, tid);
-        if (db == DEC_PACKED)
+            la.skip();
+        } else {
+            la.issue(sa, kleft, tid);
+        }
+        if (sm.dec_b[q % DEC] == DEC_PACKED) {
             load_packed_tile<T, BN, BK, THREADS>(
                 sb, p.pack_b + ((int64_t)j * p.kt + kb) * (BN * BK), tid);
-        else
-            load_raw_tile<T, BN, BK, THREADS>(sb, p.B, p.ldb, j * BN, kb * BK, p.n, p.k,
-                                              p.b_contig_n, tid);
-    }
-
-    static __device__ __forceinline__ void compute(const T *As, const T *Bs, T (&acc)[TM][TN],
-                                                   int tx, int ty)
-    {
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            T a[TM], b[TN];
-            lds16<T>(a, As + tile_off<T, BK>(tx * CH, kk));
-            lds16<T>(a + CH, As + tile_off<T, BK>(BM / 2 + tx * CH, kk));
-            lds16<T>(b, Bs + tile_off<T, BK>(ty * CH, kk));
-            lds16<T>(b + CH, Bs + tile_off<T, BK>(BN / 2 + ty * CH, kk));
-#pragma unroll
-            for (int ii = 0; ii < TM; ++ii)
-#pragma unroll
-                for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fma(a[ii], b[jj], acc[ii][jj]);
+            lb.skip();
+        } else {
+            lb.issue(sb, kleft, tid);
         }
     }
 
+    // acc += As^T Bs over the BK rows of one stage.  Fragment addresses are a per-thread base
+    // plus kk * P; the loop is unrolled UNROLL rows at a time to bound the code size.
+    static constexpr int UNROLL = BK < 8 ? BK : 8;
+    static __device__ __forceinline__ void compute(const T *As, const T *Bs, T (&acc)[TM][TN],
+                                                   int tx, int ty)
+    {
+        using LA = TileLayout<T, BM, BK>;
+        using LB = TileLayout<T, BN, BK>;
+        const T *a0 = As + LA::off(tx * CH, 0);
+        const T *a1 = As + LA::off(BM / 2 + tx * CH, 0);
+        const T *b0 = Bs + LB::off(ty * CH, 0);
+        const T *b1 = Bs + LB::off(BN / 2 + ty * CH, 0);
+#pragma unroll 1
+        for (int k0 = 0; k0 < BK; k0 += UNROLL) {
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int kk = k0 + u;
+                T a[TM], b[TN];
+                lds16<T>(a, a0 + kk * LA::P);
+                lds16<T>(a + CH, a1 + kk * LA::P);
+                lds16<T>(b, b0 + kk * LB::P);
+                lds16<T>(b + CH, b1 + kk * LB::P);
+#pragma unroll
+                for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+                    for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fma(a[ii], b[jj], acc[ii][jj]);
+            }
+        }
+    }
+
+    // Publishes the tiles this CTA produced at local k-block it (thread 0 only).
+    static __device__ __forceinline__ void publish_produced(const GemmParams<T> &p,
+                                                            const GemmSmem<T> &sm, int i, int j,
+                                                            int kb0, int it)
+    {
+        if (sm.dec_a[it % DEC] == DEC_PRODUCE)
+            publish(p.state_a + (int64_t)i * p.kt + kb0 + it, p.epoch);
+        if (sm.dec_b[it % DEC] == DEC_PRODUCE)
+            publish(p.state_b + (int64_t)j * p.kt + kb0 + it, p.epoch);
+    }
+
     // Accumulates op(A)[tile rows, kb0*BK : kb1*BK] * op(B)[..., tile cols] into acc, packing
-    // operand tiles on the way where this CTA won the claim.
-    static __device__ void run_segment(const GemmParams<T> &p, GemmSmem<T> &sm, int t, int kb0,
-                                       int kb1, T (&acc)[TM][TN])
+    // operand tiles on the way where this tile is a producer.
+    static __device__ void run_segment(const GemmParams<T> &p, GemmSmem<T> &sm, int i, int j,
+                                       int kb0, int kb1, T (&acc)[TM][TN])
     {
         const int tid = threadIdx.x;
         const int tx = tid % TX, ty = tid / TX;
-        const int i = t % p.mt, j = t / p.mt;
         const int nkb = kb1 - kb0;
 
 #pragma unroll
@@ -281,27 +423,33 @@ template <typename T> struct Kernel {
 #pragma unroll
             for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = T(0);
 
+        LoadA la;
+        LoadB lb;
+        la.init(p.A, p.lda, i * BM, kb0 * BK, p.m, tid);
+        lb.init(p.B, p.ldb, j * BN, kb0 * BK, p.n, tid);
+
         if (tid == 0) {
-            unsigned long long oa[STAGES], ob[STAGES];
+            // a panel whose producer finished it whole needs no per-k-block look-ups
+            const bool fa = need_word(p.mode_a, j == 0, 0) &&
+                            ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) == ready_value(p.epoch);
+            const bool fb = need_word(p.mode_b, i == 0, 0) &&
+                            ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) == ready_value(p.epoch);
+            sm.full_a = fa;
+            sm.full_b = fb;
+            Words w[STAGES];
 #pragma unroll
-            for (int q = 0; q < STAGES; ++q) {
-                if (q < nkb) {
-                    oa[q] = fetch(p.mode_a, p.state_a + (int64_t)i * p.kt + kb0 + q, p.epoch);
-                    ob[q] = fetch(p.mode_b, p.state_b + (int64_t)j * p.kt + kb0 + q, p.epoch);
-                }
-            }
+            for (int q = 0; q < STAGES; ++q)
+                if (q < nkb) w[q] = fetch_words(p, sm, i, j, kb0 + q);
+            bool acq = fa || fb;
 #pragma unroll
-            for (int q = 0; q < STAGES; ++q) {
-                if (q < nkb) {
-                    sm.dec_a[q] = classify(p.mode_a, oa[q], p.epoch);
-                    sm.dec_b[q] = classify(p.mode_b, ob[q], p.epoch);
-                }
-            }
+            for (int q = 0; q < STAGES; ++q)
+                if (q < nkb) acq |= store_decisions(p, sm, i, j, w[q], q);
+            if (acq) fence_acquire();
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < STAGES - 1; ++q) {
-            if (q < nkb) issue(p, sm, i, j, kb0 + q, q, tid);
+            if (q < nkb) issue(p, sm, la, lb, i, j, kb0 + q, q, tid);
             cp_async_commit();
         }
 
@@ -309,12 +457,6 @@ template <typename T> struct Kernel {
             cp_async_wait<STAGES - 2>();
             __syncthreads();
             const int stage = it % STAGES;
-            if (tid == 0 && it > 0) {
-                if (sm.dec_a[(it - 1) % DEC] == DEC_PRODUCE)
-                    publish(p.state_a + (int64_t)i * p.kt + kb0 + it - 1, p.epoch);
-                if (sm.dec_b[(it - 1) % DEC] == DEC_PRODUCE)
-                    publish(p.state_b + (int64_t)j * p.kt + kb0 + it - 1, p.epoch);
-            }
             if (sm.dec_a[it % DEC] == DEC_PRODUCE)
                 store_packed_tile<T, BM, BK, THREADS>(
                     p.pack_a + ((int64_t)i * p.kt + kb0 + it) * (BM * BK), sm.a[stage], tid);
@@ -322,37 +464,41 @@ template <typename T> struct Kernel {
                 store_packed_tile<T, BN, BK, THREADS>(
                     p.pack_b + ((int64_t)j * p.kt + kb0 + it) * (BN * BK), sm.b[stage], tid);
             const int q = it + STAGES - 1;
-            if (q < nkb) issue(p, sm, i, j, kb0 + q, q, tid);
+            if (q < nkb) issue(p, sm, la, lb, i, j, kb0 + q, q, tid);
             cp_async_commit();
-            // claims for k-block it+STAGES: fetched now, classified after this block's compute
+            // ready words for k-block it+STAGES: loaded now, used after this block's compute
             const bool ahead = (tid == 0) && (it + STAGES < nkb);
-            unsigned long long oa = 0, ob = 0;
-            if (ahead) {
-                oa = fetch(p.mode_a, p.state_a + (int64_t)i * p.kt + kb0 + it + STAGES, p.epoch);
-                ob = fetch(p.mode_b, p.state_b + (int64_t)j * p.kt + kb0 + it + STAGES, p.epoch);
-            }
+            Words w{0ull, 0ull};
+            if (ahead) w = fetch_words(p, sm, i, j, kb0 + it + STAGES);
             compute(sm.a[stage], sm.b[stage], acc, tx, ty);
-            if (ahead) {
-                sm.dec_a[(it + STAGES) % DEC] = classify(p.mode_a, oa, p.epoch);
-                sm.dec_b[(it + STAGES) % DEC] = classify(p.mode_b, ob, p.epoch);
+            if (tid == 0) {
+                if (ahead && store_decisions(p, sm, i, j, w, it + STAGES)) fence_acquire();
+                // the pack stores of the previous k-block were ordered by this iteration's
+                // barrier and have drained during the compute
+                if (it > 0) publish_produced(p, sm, i, j, kb0, it - 1);
             }
         }
         cp_async_wait<0>();
         __syncthreads();
         if (tid == 0 && nkb > 0) {
-            if (sm.dec_a[(nkb - 1) % DEC] == DEC_PRODUCE)
-                publish(p.state_a + (int64_t)i * p.kt + kb0 + nkb - 1, p.epoch);
-            if (sm.dec_b[(nkb - 1) % DEC] == DEC_PRODUCE)
-                publish(p.state_b + (int64_t)j * p.kt + kb0 + nkb - 1, p.epoch);
+            publish_produced(p, sm, i, j, kb0, nkb - 1);
+            // a producer that covered its whole panel publishes the panel as complete
+            if (kb0 == 0 && kb1 == p.kt) {
+                if (p.mode_a == MODE_FIP && j == 0)
+                    publish(p.state_a + (int64_t)p.mt * p.kt + i, p.epoch);
+                if (p.mode_b == MODE_FIP && i == 0)
+                    publish(p.state_b + (int64_t)p.nt * p.kt + j, p.epoch);
+            }
         }
     }
 
     // C[tile] := alpha*acc + beta*C[tile]; C is not read when beta == 0.
-    static __device__ void epilogue(const GemmParams<T> &p, int t, const T (&acc)[TM][TN])
+    static __device__ void epilogue(const GemmParams<T> &p, int i, int j,
+                                    const T (&acc)[TM][TN])
     {
         const int tid = threadIdx.x;
         const int tx = tid % TX, ty = tid / TX;
-        const int m0 = (t % p.mt) * BM, n0 = (t / p.mt) * BN;
+        const int m0 = i * BM, n0 = j * BN;
         const bool read_c = (p.beta != T(0));
 #pragma unroll
         for (int jj = 0; jj < TN; ++jj) {
@@ -378,8 +524,8 @@ template <typename T> struct Kernel {
 
     // A split tile's partial sum: store it, count arrivals, and let the last arrival add the
     // partials of all segments in k order and write C.
-    static __device__ void fixup(const GemmParams<T> &p, GemmSmem<T> &sm, int t, int g,
-                                 int slot, T (&acc)[TM][TN])
+    static __device__ void fixup(const GemmParams<T> &p, GemmSmem<T> &sm, int t, int i, int j,
+                                 int g, int slot, T (&acc)[TM][TN])
     {
         const int tid = threadIdx.x;
         const int64_t S = p.sk_iters;
@@ -393,7 +539,8 @@ template <typename T> struct Kernel {
 #pragma unroll
         for (int ii = 0; ii < TM; ++ii)
 #pragma unroll
-            for (int jj = 0; jj < TN; ++jj) __stcg(mine + (ii * TN + jj) * THREADS + tid, acc[ii][jj]);
+            for (int jj = 0; jj < TN; ++jj)
+                __stcg(mine + (ii * TN + jj) * THREADS + tid, acc[ii][jj]);
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -419,7 +566,7 @@ template <typename T> struct Kernel {
                         acc[ii][jj] = (gg == g0) ? v : acc[ii][jj] + v;
                     }
             }
-            epilogue(p, t, acc);
+            epilogue(p, i, j, acc);
         }
         __syncthreads();
     }
@@ -429,8 +576,10 @@ template <typename T> struct Kernel {
         const int g = blockIdx.x;
         T acc[TM][TN];
         for (int t = g; t < p.dp_tiles; t += p.grid) {
-            run_segment(p, sm, t, 0, p.kt, acc);
-            epilogue(p, t, acc);
+            int i, j;
+            tile_coords(t, p.mt, p.nt, i, j);
+            run_segment(p, sm, i, j, 0, p.kt, acc);
+            epilogue(p, i, j, acc);
             __syncthreads();
         }
         if (p.sk_iters > 0) {
@@ -440,15 +589,18 @@ template <typename T> struct Kernel {
             while (q < hi) {
                 const int u = static_cast<int>(q / p.kt);
                 const int t = p.dp_tiles + u;
+                int i, j;
+                tile_coords(t, p.mt, p.nt, i, j);
                 const int kb0 = static_cast<int>(q % p.kt);
                 const int64_t rest = hi - q;
-                const int kb1 = (rest < (int64_t)(p.kt - kb0)) ? kb0 + static_cast<int>(rest) : p.kt;
-                run_segment(p, sm, t, kb0, kb1, acc);
+                const int kb1 =
+                    (rest < (int64_t)(p.kt - kb0)) ? kb0 + static_cast<int>(rest) : p.kt;
+                run_segment(p, sm, i, j, kb0, kb1, acc);
                 if (kb0 == 0 && kb1 == p.kt) {
-                    epilogue(p, t, acc);
+                    epilogue(p, i, j, acc);
                     __syncthreads();
                 } else {
-                    fixup(p, sm, t, g, (u == first_u) ? 0 : 1, acc);
+                    fixup(p, sm, t, i, j, g, (u == first_u) ? 0 : 1, acc);
                 }
                 q += kb1 - kb0;
             }
@@ -456,44 +608,51 @@ template <typename T> struct Kernel {
     }
 };
 
-template <typename T>
+template <typename T, bool ACONTIG, bool BCONTIG>
 __global__ void __launch_bounds__(TileCfg<T>::THREADS, TileCfg<T>::MIN_BLOCKS)
     gemm_kernel(const GemmParams<T> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     GemmSmem<T> &sm = *reinterpret_cast<GemmSmem<T> *>(smem_raw);
-    Kernel<T>::run(p, sm);
+    Kernel<T, ACONTIG, BCONTIG>::run(p, sm);
 }
 
-// Pack kernel of the pack-then-compute variant: block b packs one (panel, k-block) tile,
-// A tiles first, through the same shared-memory staging as the GEMM kernel.
-template <typename T>
+// One (panel, k-block) tile of the pack-then-compute variant: raw load into shared memory,
+// then the same image the fused kernel writes.
+template <typename T, int BX, bool CONTIG>
+__device__ __forceinline__ void pack_one(const T *g, int64_t ld, int panel, int kb, int x_ext,
+                                         int k_ext, T *dst, T *tile, int tid)
+{
+    using Cfg = TileCfg<T>;
+    RawLoader<T, BX, Cfg::BK, Cfg::THREADS, CONTIG> l;
+    l.init(g, ld, panel * BX, kb * Cfg::BK, x_ext, tid);
+    l.issue(smem_addr(tile), k_ext - kb * Cfg::BK, tid);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    store_packed_tile<T, BX, Cfg::BK, Cfg::THREADS>(dst, tile, tid);
+}
+
+// Pack kernel of the pack-then-compute variant: block b packs one tile, A tiles first.
+template <typename T, bool ACONTIG, bool BCONTIG>
 __global__ void __launch_bounds__(TileCfg<T>::THREADS) pack_kernel(const PackParams<T> p)
 {
     using Cfg = TileCfg<T>;
-    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK, THREADS = Cfg::THREADS;
+    constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
     constexpr int BX = BM > BN ? BM : BN;
-    __shared__ __align__(128) T tile[BX * BK];
+    __shared__ __align__(128) T tile[TileLayout<T, BX, BK>::ELEMS];
     const int tid = threadIdx.x;
     const int64_t a_tiles = (int64_t)p.mt * p.kt;
     const int64_t b = blockIdx.x;
     if (b < a_tiles) {
         const int i = static_cast<int>(b / p.kt), kb = static_cast<int>(b % p.kt);
-        load_raw_tile<T, BM, BK, THREADS>(smem_addr(tile), p.A, p.lda, i * BM, kb * BK, p.m, p.k,
-                                          p.a_contig_m, tid);
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
-        store_packed_tile<T, BM, BK, THREADS>(p.pack_a + b * (BM * BK), tile, tid);
+        pack_one<T, BM, ACONTIG>(p.A, p.lda, i, kb, p.m, p.k, p.pack_a + b * (BM * BK), tile,
+                                 tid);
     } else {
         const int64_t bb = b - a_tiles;
         const int j = static_cast<int>(bb / p.kt), kb = static_cast<int>(bb % p.kt);
-        load_raw_tile<T, BN, BK, THREADS>(smem_addr(tile), p.B, p.ldb, j * BN, kb * BK, p.n, p.k,
-                                          p.b_contig_n, tid);
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
-        store_packed_tile<T, BN, BK, THREADS>(p.pack_b + bb * (BN * BK), tile, tid);
+        pack_one<T, BN, BCONTIG>(p.B, p.ldb, j, kb, p.n, p.k, p.pack_b + bb * (BN * BK), tile,
+                                 tid);
     }
 }
 
@@ -515,30 +674,54 @@ template <typename T> inline size_t gemm_smem_bytes()
     return sizeof(GemmSmem<T>);
 }
 
-template <typename T> cudaError_t launch_gemm_impl(const GemmParams<T> &p, cudaStream_t s)
+template <typename T, bool AC, bool BC> cudaError_t configure_gemm()
 {
     static bool configured = false;
-    const size_t smem = gemm_smem_bytes<T>();
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    gemm_kernel<T><<<p.grid, TileCfg<T>::THREADS, smem, s>>>(p);
+    if (configured) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<T, AC, BC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(gemm_smem_bytes<T>()));
+    if (e == cudaSuccess) configured = true;
+    return e;
+}
+
+template <typename T, bool AC, bool BC>
+cudaError_t launch_gemm_t(const GemmParams<T> &p, cudaStream_t s)
+{
+    cudaError_t e = configure_gemm<T, AC, BC>();
+    if (e != cudaSuccess) return e;
+    gemm_kernel<T, AC, BC><<<p.grid, TileCfg<T>::THREADS, gemm_smem_bytes<T>(), s>>>(p);
     return cudaGetLastError();
 }
 
+template <typename T> cudaError_t launch_gemm_impl(const GemmParams<T> &p, cudaStream_t s)
+{
+    if (p.a_contig_m)
+        return p.b_contig_n ? launch_gemm_t<T, true, true>(p, s)
+                            : launch_gemm_t<T, true, false>(p, s);
+    return p.b_contig_n ? launch_gemm_t<T, false, true>(p, s)
+                        : launch_gemm_t<T, false, false>(p, s);
+}
+
+template <typename T, bool AC, bool BC> int blocks_per_sm_one()
+{
+    if (configure_gemm<T, AC, BC>() != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_kernel<T, AC, BC>,
+                                                      TileCfg<T>::THREADS,
+                                                      gemm_smem_bytes<T>()) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+// Resident CTAs per SM: the minimum over the four operand-order instantiations, so the grid
+// (and hence the split points and the result bits) does not depend on the operand order.
 template <typename T> int gemm_blocks_per_sm_impl()
 {
-    const size_t smem = gemm_smem_bytes<T>();
-    cudaFuncSetAttribute(gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gemm_kernel<T>, TileCfg<T>::THREADS,
-                                                      smem) != cudaSuccess)
-        return 0;
+    int n = blocks_per_sm_one<T, true, true>();
+    n = std::min(n, blocks_per_sm_one<T, true, false>());
+    n = std::min(n, blocks_per_sm_one<T, false, true>());
+    n = std::min(n, blocks_per_sm_one<T, false, false>());
     return n;
 }
 
@@ -546,7 +729,19 @@ template <typename T> cudaError_t launch_pack_impl(const PackParams<T> &p, cudaS
 {
     const int64_t blocks = (int64_t)(p.mt + p.nt) * p.kt;
     if (blocks <= 0) return cudaSuccess;
-    pack_kernel<T><<<static_cast<unsigned int>(blocks), TileCfg<T>::THREADS, 0, s>>>(p);
+    const unsigned int nb = static_cast<unsigned int>(blocks);
+    const int th = TileCfg<T>::THREADS;
+    if (p.a_contig_m) {
+        if (p.b_contig_n)
+            pack_kernel<T, true, true><<<nb, th, 0, s>>>(p);
+        else
+            pack_kernel<T, true, false><<<nb, th, 0, s>>>(p);
+    } else {
+        if (p.b_contig_n)
+            pack_kernel<T, false, true><<<nb, th, 0, s>>>(p);
+        else
+            pack_kernel<T, false, false><<<nb, th, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
