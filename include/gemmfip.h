@@ -13,7 +13,8 @@
  * contiguous tile layout the first time a CTA computes with it, in the same pass ("fused-in
  * packing"); later CTAs load the packed copy.  Which operands are worth packing follows the
  * option table of Sec. 3.3 (pack A only if the result has more than one tile column, pack
- * B only if it has more than one tile row).  The two comparison variants of Sec. 2.3-2.4
+ * B only if it has more than one tile row), and packing is used only when some tiles run
+ * after the first wave of CTAs, since only those can read a finished packed copy.  The two comparison variants of Sec. 2.3-2.4
  * are exported as well: a direct-strided kernel that never packs (the SUP path) and a
  * pack-then-compute pair of launches (the conventional path).  All three produce
  * bit-identical results for the same arguments on the same GPU.
@@ -64,7 +65,8 @@ typedef struct gfip_handle_s *gfip_handle_t;
 #define GFIP_STATUS_BAD_SEGMENT 0x1u   /* a split tile saw more partial sums than planned */
 
 /* Pack policies for gfip_set_pack_policy(). */
-#define GFIP_PACK_AUTO 0        /* Sec. 3.3 option table: pack A iff > 1 tile column, B iff > 1 tile row */
+#define GFIP_PACK_AUTO 0        /* Sec. 3.3 option table: pack A iff > 1 tile column, B iff > 1 tile
+                                   row, and only when some tiles run after the first wave of CTAs  */
 #define GFIP_PACK_NONE 1        /* never pack (the fused kernel then equals the direct variant)          */
 #define GFIP_PACK_A 2           /* pack A panels only                                                   */
 #define GFIP_PACK_B 3           /* pack B panels only                                                   */

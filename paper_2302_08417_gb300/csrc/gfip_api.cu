@@ -152,10 +152,16 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
         case GFIP_PACK_BOTH:
             pl.mode_a = pl.mode_b = gfip::MODE_FIP;
             break;
-        default:  // AUTO: an A panel is reused only across tile columns, a B panel across rows
-            pl.mode_a = (pl.nt > 1) ? gfip::MODE_FIP : gfip::MODE_RAW;
-            pl.mode_b = (pl.mt > 1) ? gfip::MODE_FIP : gfip::MODE_RAW;
+        default: {
+            // AUTO: Sec. 3.3's table (an A panel is reused only across tile columns, a B
+            // panel only across tile rows), read for a GPU: a packed copy pays off only for
+            // tiles that run after its producer, i.e. when there are more tiles than one wave
+            // of CTAs; tiles running side by side with the producer read the raw operand
+            const bool later = pl.tiles > pl.grid;
+            pl.mode_a = (pl.nt > 1 && later) ? gfip::MODE_FIP : gfip::MODE_RAW;
+            pl.mode_b = (pl.mt > 1 && later) ? gfip::MODE_FIP : gfip::MODE_RAW;
             break;
+        }
         }
         break;
     }

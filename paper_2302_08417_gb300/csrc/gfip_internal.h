@@ -16,11 +16,33 @@ enum OperandMode : int {
 };
 
 // Tile shape of one element type.  The CTA computes a BM x BN tile of C, stepping through
-// k in blocks of BK; 256 threads each own a (2*CH) x (2*CH) register micro-tile.
+// k in blocks of BK; each thread owns a (2*CH) x (2*CH) register micro-tile (CH = elements
+// per 16 bytes).
 template <typename T> struct TileCfg;
 
+// FP64: the DFMA pipe (2 lanes per clock per SM) is the bound at every size, so small tiles
+// cost no throughput and give fine-grained work units that keep all SMs busy.
+#ifndef GFIP_F64_BM
+#define GFIP_F64_BM 32
+#endif
+#ifndef GFIP_F64_BN
+#define GFIP_F64_BN 32
+#endif
+#ifndef GFIP_F64_MIN_BLOCKS
+#define GFIP_F64_MIN_BLOCKS 6
+#endif
+#ifndef GFIP_F64_UNROLL
+#define GFIP_F64_UNROLL 2
+#endif
+// A CTA runs at least 4 warps, one per SM sub-partition (each has its own FP64 unit), with
+// 4 x 2 micro-tiles for tiles of up to 1024 elements and 4 x 4 above.
 template <> struct TileCfg<double> {
-    static constexpr int BM = 64, BN = 64, BK = 16, THREADS = 256, STAGES = 4, MIN_BLOCKS = 2;
+    static constexpr int BM = GFIP_F64_BM, BN = GFIP_F64_BN, BK = 16;
+    static constexpr int NCN = (BM * BN / 128 >= 16) ? 2 : 1;       // 4 x 4 or 4 x 2 per thread
+    static constexpr int THREADS = BM * BN / (4 * 2 * NCN) < 128 ? 128 : BM * BN / (4 * 2 * NCN);
+    static constexpr int STAGES = 3;
+    static constexpr int MIN_BLOCKS = GFIP_F64_MIN_BLOCKS;
+    static constexpr int UNROLL = GFIP_F64_UNROLL;  // k rows per unrolled compute step
 };
 #ifndef GFIP_F32_MIN_BLOCKS
 #define GFIP_F32_MIN_BLOCKS 2
@@ -31,8 +53,10 @@ template <> struct TileCfg<double> {
 #ifndef GFIP_F32_BK
 #define GFIP_F32_BK 32
 #endif
+
 template <> struct TileCfg<float> {
-    static constexpr int BM = 128, BN = 128, BK = GFIP_F32_BK, THREADS = 256;
+    static constexpr int BM = 128, BN = 128, BK = GFIP_F32_BK, THREADS = 256, NCN = 2;
+    static constexpr int UNROLL = 8;
     static constexpr int STAGES = GFIP_F32_STAGES, MIN_BLOCKS = GFIP_F32_MIN_BLOCKS;
 };
 

@@ -102,21 +102,30 @@ template <typename T, int BX, int BK> struct TileLayout {
 // k-block costs one pointer increment plus one copy per element.  Out-of-range elements are
 // zero-filled (the fringe padding of Sec. 2.2).
 //   CONTIG: x = tid % BX, kk = tid / BX + r * (THREADS / BX): a warp reads 32 consecutive x.
-//   else:   a warp covers 4 consecutive x by 8 consecutive k; x = 4*warp + lane/8 + 32*(r%G),
-//           kk = lane%8 + 8*(r/G), G = BX/32: four runs of 8 contiguous elements per warp.
+//   else:   a warp covers blocks of 4 consecutive x by 8 consecutive k (four runs of 8
+//           contiguous elements); block b = warp + r * NW (NW warps) sits at
+//           x = 4 * (b % XB) + lane/8, kk = 8 * (b / XB) + lane%8 with XB = BX/4.  Because NW
+//           divides XB, element r is element 0 shifted by the constants DX(r), DK(r).
 template <typename T, int BX, int BK, int THREADS, bool CONTIG> struct RawLoader {
     using L = TileLayout<T, BX, BK>;
     static constexpr int PER = BX * BK / THREADS;
-    static constexpr int G = BX / 32;
+    static constexpr int NW = THREADS / 32;
+    static constexpr int XB = BX / 4;
     static_assert(PER * THREADS == BX * BK, "tile must divide over the threads");
     static_assert(!CONTIG || THREADS % BX == 0, "contiguous pattern needs THREADS % BX == 0");
-    static_assert(CONTIG || (THREADS == 256 && BK % 8 == 0 && PER == G * (BK / 8)),
-                  "transposed pattern assumes 8 warps");
+    static_assert(CONTIG || (XB % NW == 0 && BK % 8 == 0 && PER * NW == XB * (BK / 8)),
+                  "transposed pattern needs the warps to divide the x blocks");
+    static_assert(L::W % (4 * NW) == 0 || (4 * NW) % L::W == 0,
+                  "a warp's x span and a 128-byte segment must nest");
+    static constexpr int NG = XB / NW;  // distinct x offsets: element r is in x group GX(r)
+    static __device__ __forceinline__ constexpr int GX(int r) { return ((r * NW) % XB) / NW; }
+    static __device__ __forceinline__ constexpr int DX(int r) { return 4 * NW * GX(r); }
+    static __device__ __forceinline__ constexpr int DK(int r) { return 8 * ((r * NW) / XB); }
 
     const T *g;       // operand base (a valid address for zero-filled copies)
     const T *p;       // this thread's element 0 at the next k-block to issue
     int64_t ld;
-    uint32_t xok;     // bit r (CONTIG: bit 0): x of element r lies inside the operand
+    uint32_t xok;     // bit GX(r): x of element r lies inside the operand (CONTIG: bit 0 only)
     int kk0;          // kk of element 0
     uint32_t s0;      // shared-memory byte offset (within a stage) of element 0
 
@@ -138,8 +147,8 @@ template <typename T, int BX, int BK, int THREADS, bool CONTIG> struct RawLoader
             p = g + (int64_t)(k0 + kk0) + (int64_t)(x0 + x) * ld;
             xok = 0;
 #pragma unroll
-            for (int r = 0; r < G; ++r)
-                if (x0 + x + 32 * r < x_ext) xok |= 1u << r;
+            for (int gx = 0; gx < NG; ++gx)
+                if (x0 + x + 4 * NW * gx < x_ext) xok |= 1u << gx;
             s0 = L::off(x, kk0) * sizeof(T);
         }
     }
@@ -161,11 +170,13 @@ template <typename T, int BX, int BK, int THREADS, bool CONTIG> struct RawLoader
         } else {
 #pragma unroll
             for (int r = 0; r < PER; ++r) {
-                const int gx = r % G, gk = r / G;
-                const bool ok = ((xok >> gx) & 1u) && (kk0 + 8 * gk < kleft);
-                const T *src = ok ? p + (int64_t)(32 * gx) * ld + 8 * gk : g;
-                // +32 x = +32/W segments; +8 kk = +8 rows
-                const uint32_t soff = s0 + ((32 / L::W) * gx * L::SEG + 8 * gk * L::P) * sizeof(T);
+                const bool ok = ((xok >> GX(r)) & 1u) && (kk0 + DK(r) < kleft);
+                const T *src = ok ? p + (int64_t)DX(r) * ld + DK(r) : g;
+                // x and x + DX(r) lie in the same 128-byte column position when DX(r) is a
+                // multiple of W, or DX(r) < W apart in the same segment: either way the
+                // layout offset moves by a constant
+                const uint32_t soff =
+                    s0 + ((DX(r) / L::W) * L::SEG + (DX(r) % L::W) + DK(r) * L::P) * sizeof(T);
                 cp_async_elem<sizeof(T)>(sdst + soff, src, ok);
             }
             p += BK;
@@ -288,9 +299,13 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
     static constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
     static constexpr int THREADS = Cfg::THREADS, STAGES = Cfg::STAGES;
     static constexpr int CH = 16 / static_cast<int>(sizeof(T));
-    static constexpr int TM = 2 * CH, TN = 2 * CH;  // register micro-tile
+    // register micro-tile: NCM (NCN) 16-byte chunks along m (n), the second chunk half a tile
+    // away from the first
+    static constexpr int NCM = 2, NCN = Cfg::NCN;
+    static constexpr int TM = NCM * CH, TN = NCN * CH;
     static constexpr int TX = BM / TM;               // threads along m
     static_assert(TX * (BN / TN) == THREADS, "thread grid must cover the tile");
+    static_assert(NCN == 1 || NCN == 2, "one or two chunks along n");
     static constexpr int DEC = 2 * STAGES;
     using LoadA = RawLoader<T, BM, BK, THREADS, ACONTIG>;
     using LoadB = RawLoader<T, BN, BK, THREADS, BCONTIG>;
@@ -370,7 +385,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
 
     // acc += As^T Bs over the BK rows of one stage.  Fragment addresses are a per-thread base
     // plus kk * P; the loop is unrolled UNROLL rows at a time to bound the code size.
-    static constexpr int UNROLL = BK < 8 ? BK : 8;
+    static constexpr int UNROLL = BK < Cfg::UNROLL ? BK : Cfg::UNROLL;
     static __device__ __forceinline__ void compute(const T *As, const T *Bs, T (&acc)[TM][TN],
                                                    int tx, int ty)
     {
@@ -379,7 +394,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
         const T *a0 = As + LA::off(tx * CH, 0);
         const T *a1 = As + LA::off(BM / 2 + tx * CH, 0);
         const T *b0 = Bs + LB::off(ty * CH, 0);
-        const T *b1 = Bs + LB::off(BN / 2 + ty * CH, 0);
+        const T *b1 = Bs + LB::off((NCN == 2 ? BN / 2 : 0) + ty * CH, 0);
 #pragma unroll 1
         for (int k0 = 0; k0 < BK; k0 += UNROLL) {
 #pragma unroll
@@ -389,7 +404,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
                 lds16<T>(a, a0 + kk * LA::P);
                 lds16<T>(a + CH, a1 + kk * LA::P);
                 lds16<T>(b, b0 + kk * LB::P);
-                lds16<T>(b + CH, b1 + kk * LB::P);
+                if (NCN == 2) lds16<T>(b + CH, b1 + kk * LB::P);
 #pragma unroll
                 for (int ii = 0; ii < TM; ++ii)
 #pragma unroll
@@ -423,6 +438,16 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
 #pragma unroll
             for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = T(0);
 
+        // the segment that ends the tile's k loop will read C: warm L2 with it now
+        if (kb1 == p.kt && p.beta != T(0)) {
+            constexpr int LINES = 128 / static_cast<int>(sizeof(T));  // elements per line
+            constexpr int PER_COL = (BM + LINES - 1) / LINES;
+            for (int e = tid; e < BN * PER_COL; e += THREADS) {
+                const int col = j * BN + e / PER_COL, row = i * BM + (e % PER_COL) * LINES;
+                if (col < p.n && row < p.m)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(p.C + row + (int64_t)col * p.ldc));
+            }
+        }
         LoadA la;
         LoadB lb;
         la.init(p.A, p.lda, i * BM, kb0 * BK, p.m, tid);
@@ -492,7 +517,10 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
         }
     }
 
-    // C[tile] := alpha*acc + beta*C[tile]; C is not read when beta == 0.
+    // C[tile] := alpha*acc + beta*C[tile]; C is not read when beta == 0.  A column's C values
+    // are all loaded before any of them is stored, so their load latencies overlap instead of
+    // queueing behind the stores (the stores could alias later loads as far as the compiler
+    // knows).
     static __device__ void epilogue(const GemmParams<T> &p, int i, int j,
                                     const T (&acc)[TM][TN])
     {
@@ -502,15 +530,21 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
         const bool read_c = (p.beta != T(0));
 #pragma unroll
         for (int jj = 0; jj < TN; ++jj) {
-            const int col = n0 + ty * CH + (jj % CH) + (jj / CH) * (BN / 2);
+            const int col = n0 + ty * CH + (jj % CH) + (jj / CH) * (BN / NCN);
             if (col >= p.n) continue;
             T *ccol = p.C + (int64_t)col * p.ldc;
+            T c[TM];
+#pragma unroll
+            for (int ii = 0; ii < TM; ++ii) {
+                const int row = m0 + tx * CH + (ii % CH) + (ii / CH) * (BM / 2);
+                c[ii] = (read_c && row < p.m) ? ccol[row] : T(0);
+            }
 #pragma unroll
             for (int ii = 0; ii < TM; ++ii) {
                 const int row = m0 + tx * CH + (ii % CH) + (ii / CH) * (BM / 2);
                 if (row >= p.m) continue;
                 T v = p.alpha * acc[ii][jj];
-                if (read_c) v = fma(p.beta, ccol[row], v);
+                if (read_c) v = fma(p.beta, c[ii], v);
                 ccol[row] = v;
             }
         }
@@ -554,17 +588,36 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
         }
         __syncthreads();
         if (sm.flag) {
-            for (int gg = g0; gg <= g1; ++gg) {
-                const int64_t lo = S * gg / G;
-                const int gslot = (lo / p.kt == u) ? 0 : 1;
-                const T *src = p.partial + (int64_t)(2 * gg + gslot) * (BM * BN);
+            // add the segments' partial sums in k order; the loads of up to INFL segments are
+            // issued before any of their adds so their latencies overlap
+            constexpr int NV = TM * TN;
+            constexpr int CHK = NV;                          // values per pass
+            constexpr int INFL = NV <= 8 ? 4 : (NV <= 16 ? 2 : 1);  // segments in flight
+            T *flat = &acc[0][0];
 #pragma unroll
-                for (int ii = 0; ii < TM; ++ii)
+            for (int c0 = 0; c0 < NV; c0 += CHK) {
+                for (int gg = g0; gg <= g1; gg += INFL) {
+                    T v[INFL][CHK];
 #pragma unroll
-                    for (int jj = 0; jj < TN; ++jj) {
-                        const T v = __ldcg(src + (ii * TN + jj) * THREADS + tid);
-                        acc[ii][jj] = (gg == g0) ? v : acc[ii][jj] + v;
+                    for (int s = 0; s < INFL; ++s) {
+                        const int gs = gg + s;
+                        if (gs > g1) break;
+                        const int64_t lo = S * gs / G;
+                        const int gslot = (lo / p.kt == u) ? 0 : 1;
+                        const T *src = p.partial + (int64_t)(2 * gs + gslot) * (BM * BN);
+#pragma unroll
+                        for (int e = 0; e < CHK; ++e)
+                            v[s][e] = __ldcg(src + (c0 + e) * THREADS + tid);
                     }
+#pragma unroll
+                    for (int s = 0; s < INFL; ++s) {
+                        const int gs = gg + s;
+                        if (gs > g1) break;
+#pragma unroll
+                        for (int e = 0; e < CHK; ++e)
+                            flat[c0 + e] = (gs == g0) ? v[s][e] : flat[c0 + e] + v[s][e];
+                    }
+                }
             }
             epilogue(p, i, j, acc);
         }
