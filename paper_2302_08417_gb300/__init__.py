@@ -2,7 +2,8 @@
 
 ``C := alpha*op(A)*op(B) + beta*C`` on BLAS column-major strided operands, computed by the
 CUDA library ``_build/libgemmfip.so`` behind the C ABI of ``include/gemmfip.h``.  The
-binding in :mod:`.gemmfip` mirrors that ABI; :func:`gemm` is the PyTorch-facing call.
+binding in :mod:`.gemmfip` mirrors that ABI; :func:`gemm` is the PyTorch-facing call and
+:mod:`.autograd` its differentiable form.
 """
 from .gemmfip import (  # noqa: F401
     GemmError, Handle, gemm, load, error_string, default_handle,
