@@ -63,6 +63,7 @@ typedef struct gfip_handle_s *gfip_handle_t;
 
 /* Device status bits, reported by gfip_get_status(). */
 #define GFIP_STATUS_BAD_SEGMENT 0x1u   /* a split tile saw more partial sums than planned */
+#define GFIP_STATUS_MMA_TIMEOUT 0x2u   /* gfip_dgemm_ozaki: a pipeline wait gave up (result invalid) */
 
 /* Pack policies for gfip_set_pack_policy(). */
 #define GFIP_PACK_AUTO 0        /* Sec. 3.3 option table: pack A iff > 1 tile column, B iff > 1 tile
@@ -130,6 +131,26 @@ int gfip_sgemm_pack_then_compute(gfip_handle_t handle, char transa, char transb,
                                  int64_t n, int64_t k, float alpha, const float *A,
                                  int64_t lda, const float *B, int64_t ldb, float beta,
                                  float *C, int64_t ldc);
+
+/* ---- FP64 GEMM emulated on the tensor cores ------------------------------------------------
+ * Extension of the method (Sec. 5 lists other precisions as future work; the slicing is a
+ * pack-time transform like the 1m method of Sec. 5): C := alpha*op(A)*op(B) + beta*C in FP64,
+ * computed from exact BF16 digit products on the tcgen05 tensor cores (Ozaki splitting).
+ * Every row of op(A) and column of op(B) is scaled by a power of two and split into `slices`
+ * 6-bit integer digits (1 <= slices <= 10); the digit pairs (s, t) with s + t <= slices + 1 are
+ * multiplied on the tensor cores with exact FP32 accumulation over k-chunks of 4096, and
+ * recombined in FP64.  The result is NOT the IEEE FP64 product: its error against the exact
+ * product is bounded by about k * 2^(e_i + f_j) * 2^(-6*slices) * (slices + 5) / 4 * |alpha|
+ * plus FP64 rounding, where 2^e_i and 2^f_j bound the magnitudes in row i of op(A) and column
+ * j of op(B); slices = 9 reaches FP64-level accuracy for data of uniform magnitude.
+ * Same argument conventions, quick returns and error codes as gfip_dgemm, plus
+ * GFIP_ERR_ARG for a slice count out of range.  Needs gfip_ozaki_workspace_size() bytes of
+ * workspace.  A timeout inside the kernel raises GFIP_STATUS_MMA_TIMEOUT. */
+size_t gfip_ozaki_workspace_size(gfip_handle_t handle, int64_t m, int64_t n, int64_t k,
+                                 int slices);
+int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
+                     int64_t k, double alpha, const double *A, int64_t lda, const double *B,
+                     int64_t ldb, double beta, double *C, int64_t ldc, int slices);
 
 /* Waits for the handle's stream, then returns the OR of the device status bits
  * (GFIP_STATUS_*) raised since the previous call of this function, and clears them.

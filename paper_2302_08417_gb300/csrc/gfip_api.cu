@@ -306,6 +306,32 @@ int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_
     return GFIP_OK;
 }
 
+// Workspace of the tensor-core FP64 emulation: digit tiles and exponents after a control
+// region of at least the header (which holds the status word).
+struct OzPlan {
+    int mt = 0, nt = 0, kt = 0;
+    size_t off_ea = 0, off_eb = 0, off_sa = 0, off_sb = 0, data_bytes = 0;
+};
+
+OzPlan oz_plan(int64_t m, int64_t n, int64_t k, int slices)
+{
+    OzPlan o;
+    o.mt = static_cast<int>((m + 127) / 128);
+    o.nt = static_cast<int>((n + 127) / 128);
+    o.kt = static_cast<int>((k + 63) / 64);
+    size_t d = 0;
+    o.off_ea = d;
+    d += round_up((size_t)o.mt * 128 * sizeof(int), kAlign);
+    o.off_eb = d;
+    d += round_up((size_t)o.nt * 128 * sizeof(int), kAlign);
+    o.off_sa = d;
+    d += (size_t)slices * o.mt * o.kt * 16384;
+    o.off_sb = d;
+    d += (size_t)slices * o.nt * o.kt * 16384;
+    o.data_bytes = d;
+    return o;
+}
+
 template <typename T>
 size_t workspace_size_impl(Handle *h, char transa, char transb, int64_t m, int64_t n, int64_t k,
                            Variant v)
@@ -513,6 +539,78 @@ const char *gfip_error_string(int code)
         return "problem needs more scratch than the allocation-free routine's static array";
     default: return "unknown error";
     }
+}
+
+size_t gfip_ozaki_workspace_size(gfip_handle_t handle, int64_t m, int64_t n, int64_t k,
+                                 int slices)
+{
+    Handle *h = get(handle);
+    if (h == nullptr || m < 0 || n < 0 || k < 0 || slices < 1 || slices > 10) return 0;
+    const OzPlan o = oz_plan(m, n, k, slices);
+    return std::max(h->ctrl_bytes, kCtrlGranule) + o.data_bytes;
+}
+
+int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
+                     int64_t k, double alpha, const double *A, int64_t lda, const double *B,
+                     int64_t ldb, double beta, double *C, int64_t ldc, int slices)
+{
+    const int info = check_args(transa, transb, m, n, k, lda, ldb, ldc);
+    if (info != 0) return info;
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    if (slices < 1 || slices > 10) return GFIP_ERR_ARG;
+    h->last_launches = 0;
+    h->last_grid = 0;
+    if (m == 0 || n == 0) return GFIP_OK;
+    const bool use_ab = !(alpha == 0.0 || k == 0);
+    if (!use_ab && beta == 1.0) return GFIP_OK;
+    if (too_big(m) || too_big(n) || too_big(k)) return GFIP_ERR_SIZE;
+    if (C == nullptr) return GFIP_ERR_NULLPTR;
+    if (!use_ab) {
+        if (gfip::launch_scale<double>(C, ldc, (int)m, (int)n, beta, h->stream) != cudaSuccess)
+            return GFIP_ERR_CUDA;
+        h->last_launches = 1;
+        return GFIP_OK;
+    }
+    if (A == nullptr || B == nullptr) return GFIP_ERR_NULLPTR;
+    if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
+    const OzPlan o = oz_plan(m, n, k, slices);
+    const size_t ctrl_want = std::max(h->ctrl_bytes, kCtrlGranule);
+    if (ctrl_want + o.data_bytes > h->ws_bytes) return GFIP_ERR_WORKSPACE;
+    if (ctrl_want > h->ctrl_bytes) {
+        if (cudaMemsetAsync(h->ws + h->ctrl_bytes, 0, ctrl_want - h->ctrl_bytes, h->stream) !=
+            cudaSuccess)
+            return GFIP_ERR_CUDA;
+        h->ctrl_bytes = ctrl_want;
+    }
+    unsigned char *data = h->ws + h->ctrl_bytes;
+    gfip::OzakiParams p{};
+    p.A = A;
+    p.B = B;
+    p.C = C;
+    p.lda = lda;
+    p.ldb = ldb;
+    p.ldc = ldc;
+    p.m = (int)m;
+    p.n = (int)n;
+    p.k = (int)k;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.a_contig_rows = is_notrans(transa) ? 1 : 0;
+    p.b_contig_rows = is_notrans(transb) ? 0 : 1;
+    p.slices = slices;
+    p.mt = o.mt;
+    p.nt = o.nt;
+    p.kt = o.kt;
+    p.ea = reinterpret_cast<int *>(data + o.off_ea);
+    p.eb = reinterpret_cast<int *>(data + o.off_eb);
+    p.sa = reinterpret_cast<uint16_t *>(data + o.off_sa);
+    p.sb = reinterpret_cast<uint16_t *>(data + o.off_sb);
+    p.status = reinterpret_cast<unsigned int *>(h->ws);
+    if (gfip::launch_ozaki(p, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
+    h->last_launches = 5;
+    h->last_grid = o.mt * o.nt;
+    return GFIP_OK;
 }
 
 }  // extern "C"

@@ -99,6 +99,27 @@ template <typename T> struct PackParams {
     T *pack_b;
 };
 
+// FP64 GEMM emulated with BF16 digit products on the tensor cores (gfip_ozaki.cu).
+struct OzakiParams {
+    const double *A;
+    const double *B;
+    double *C;
+    int64_t lda, ldb, ldc;
+    int m, n, k;
+    double alpha, beta;
+    int a_contig_rows;   // 1: row i of op(A) runs along memory (transa 'N')
+    int b_contig_rows;   // 1: column j of op(B) = row j of its K-major form runs along memory ('T')
+    int slices;          // digits per element (S)
+    int mt, nt, kt;      // 128-row blocks of m and n, 64-wide k blocks
+    int *ea;             // [mt * 128] row exponents of op(A)
+    int *eb;             // [nt * 128] column exponents of op(B)
+    uint16_t *sa;        // [S][mt][kt] digit tiles of op(A), 16 KB each
+    uint16_t *sb;        // [S][nt][kt] digit tiles of op(B)
+    unsigned int *status;
+};
+cudaError_t launch_ozaki(const OzakiParams &p, cudaStream_t s);
+size_t ozaki_smem_bytes();
+
 // Launchers (defined per element type in gfip_f64.cu / gfip_f32.cu).
 template <typename T> cudaError_t launch_gemm(const GemmParams<T> &p, cudaStream_t s);
 template <typename T> cudaError_t launch_pack(const PackParams<T> &p, cudaStream_t s);

@@ -1,0 +1,493 @@
+// gfip_ozaki.cu -- FP64 GEMM emulated on the tcgen05 tensor cores with exact BF16 digit
+// products (the Ozaki splitting scheme: Ozaki, Ogita, Oishi, Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix multiplication
+// and its applications", Numer. Algorithms 59 (2012); here with BF16 digits and FP32
+// accumulation).
+//
+// Splitting (a pack-time transform, like the slicing that the GEMMFIP paper's future work,
+// Sec. 5, folds into packing): every row i of op(A) gets an exponent e_i with
+// max_p |a_ip| < 2^e_i, and every element becomes exactly
+//     a_ip = 2^e_i * (sum_{s=1..S} d_s * 2^(-6 s) + r),   |d_1| <= 64, |d_s| <= 32 (s > 1),
+// with integer digits d_s (exact in BF16) and |r| <= 2^(-6 S - 1).  Columns of op(B) are split
+// the same way with exponents f_j.  A product of two digits is an integer of at most 2^12, so
+// a sum of up to 4096 of them is an integer below 2^24 and the tensor cores' FP32
+// accumulation of such a k-chunk is exact.  The product is recombined in FP64:
+//     C_ij = alpha * 2^(e_i + f_j) * sum_{s+t <= S+1} 2^(-6(s+t)) * sum_chunks D_st + beta*C_ij,
+// dropping the digit pairs with s + t > S + 1 (triangular truncation).
+//
+// Kernel layout (one CTA per 128 x 128 tile of C, 10 warps):
+//   warp 0      producer: bulk-copies the A- and B-digit tiles (16 KB each, stored already in
+//               the swizzled shared-memory layout the MMA reads) into a 4-stage ring;
+//   warp 1      allocates tensor memory and issues tcgen05.mma (one thread) into one of two
+//               128-column FP32 accumulators, one accumulator per (digit pair, k-chunk);
+//   warps 2-9   drain a finished accumulator with tcgen05.ld and add it, scaled, into FP64
+//               registers (64 values per thread), then write C.
+// Every mbarrier wait is bounded; on a timeout the kernel raises a status bit, the roles
+// skip their remaining work, and tensor memory is released before exit.
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
+#include "gfip_internal.h"
+
+namespace gfip {
+
+namespace oz {
+
+constexpr int TM = 128;              // tile rows (M of the MMA) and digit-tile rows
+constexpr int TN = 128;              // tile cols (N of the MMA)
+constexpr int KB = 64;               // k per digit tile: 64 BF16 = one 128-byte row
+constexpr int TILE_BYTES = TM * KB * 2;  // 16 KB per digit tile (A and B alike)
+constexpr int STAGES = 4;
+constexpr int THREADS = 320;
+constexpr int EPI_WARPS = 8;
+constexpr int BETA_BITS = 6;         // bits per digit
+constexpr int KC_BLOCKS = 4096 / KB; // k-blocks per exactly accumulated chunk
+constexpr uint32_t TMEM_COLS = 256;  // two 128-column FP32 accumulators
+constexpr unsigned STATUS_TIMEOUT = 0x2u;  // mirrors GFIP_STATUS_MMA_TIMEOUT
+constexpr long long WAIT_LIMIT = 1ll << 26;  // polls before a wait gives up
+
+struct Smem {
+    uint8_t a[STAGES][TILE_BYTES];   // 1024-byte aligned (swizzle atoms)
+    uint8_t b[STAGES][TILE_BYTES];
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ bool aborted(const Smem &sm)
+{
+    return *(volatile const int *)&sm.abort != 0;
+}
+
+__device__ __forceinline__ uint32_t saddr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+// Waits for the phase with the given parity to complete; gives up after WAIT_LIMIT polls or
+// when another role has aborted.  Returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Smem &sm,
+                                          unsigned *status)
+{
+    const uint32_t a = saddr(bar);
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (aborted(sm)) return false;
+    }
+    *(volatile int *)&sm.abort = 1;
+    atomicOr(status, STATUS_TIMEOUT);
+    return false;
+}
+
+// 16 KB global -> shared bulk copy (TMA engine), completing on an mbarrier.
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle layout: 8-row
+// groups of 128-byte rows, 1024 bytes apart (stride byte offset); descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);        // start address
+    d |= (uint64_t)1 << 16;                        // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16 with BF16 A and B, FP32 D, both K-major, M = 128, N = 128.
+constexpr uint32_t IDESC = (1u << 4)                      // D: F32
+                           | (1u << 7)                    // A: BF16
+                           | (1u << 10)                   // B: BF16
+                           | ((uint32_t)(TN >> 3) << 17)  // N
+                           | ((uint32_t)(TM >> 4) << 24); // M
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Byte offset of element (r, c) (r < 128 rows, c < 64 k) in a digit tile: 8-row groups of
+// 1024 bytes; inside a group, row r%8 is 128 bytes whose 16-byte chunks are XOR-permuted by r%8.
+__device__ __forceinline__ uint32_t digit_off(int r, int c)
+{
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((c >> 3) ^ (r & 7))) << 4) +
+                      (c & 7) * 2);
+}
+
+// ---- splitting ---------------------------------------------------------------------------
+
+// Exponent of each row: e with max_p |x_rp| < 2^e (0 for an all-zero row).  Row r of the
+// operand has element (r, p) at X[r + p*ld] when contig_rows, else X[p + r*ld].
+__global__ void __launch_bounds__(256) row_exponent_kernel(const double *X, int64_t ld,
+                                                           int rows, int kdim, int contig_rows,
+                                                           int *expo)
+{
+    __shared__ double red[256];
+    const int tid = threadIdx.x;
+    const int r0 = blockIdx.x * TM;
+    double mx = 0.0;
+    if (contig_rows) {
+        // two threads per row, consecutive rows in consecutive threads
+        const int r = r0 + (tid % TM);
+        if (r < rows)
+            for (int p = tid / TM; p < kdim; p += 2) mx = fmax(mx, fabs(X[r + (int64_t)p * ld]));
+        red[tid] = mx;
+        __syncthreads();
+        if (tid < TM) {
+            mx = fmax(red[tid], red[tid + TM]);
+            if (r0 + tid < rows) {
+                int e = 0;
+                if (mx > 0.0) frexp(mx, &e);   // mx = f * 2^e, 0.5 <= f < 1  =>  mx < 2^e
+                expo[r0 + tid] = e;
+            }
+        }
+    } else {
+        // one warp per row, lanes along the contiguous k
+        const int lane = tid & 31, w = tid >> 5;
+        for (int rr = w; rr < TM; rr += 8) {
+            const int r = r0 + rr;
+            double m2 = 0.0;
+            if (r < rows)
+                for (int p = lane; p < kdim; p += 32) m2 = fmax(m2, fabs(X[p + (int64_t)r * ld]));
+            for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+            if (lane == 0 && r < rows) {
+                int e = 0;
+                if (m2 > 0.0) frexp(m2, &e);
+                expo[r] = e;
+            }
+        }
+    }
+}
+
+// Digit tiles of one 128 x 64 block: every element is scaled by 2^-e_row and split into S
+// base-64 digits by repeated scale-round-subtract (all steps exact in FP64).  Digit s of all
+// elements is staged in shared memory in the swizzled tile layout, then written out with
+// 16-byte stores.  Fringe rows and k positions give zero digits.
+__global__ void __launch_bounds__(256) split_kernel(const double *X, int64_t ld, int rows,
+                                                    int kdim, int contig_rows, int S,
+                                                    const int *expo, uint16_t *tiles,
+                                                    int row_blocks, int kblocks)
+{
+    __shared__ __align__(1024) uint8_t stage[TILE_BYTES];
+    const int tid = threadIdx.x;
+    const int rb = blockIdx.x % row_blocks, kb = blockIdx.x / row_blocks;
+    constexpr int PER = TM * KB / 256;   // 32 elements per thread
+    double rem[PER];
+    int er[PER], ec[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        int r, c;
+        if (contig_rows) {          // consecutive threads on consecutive rows
+            r = tid % TM;
+            c = tid / TM + 2 * q;
+        } else {                    // consecutive threads on consecutive k
+            c = tid % KB;
+            r = tid / KB + 4 * q;
+        }
+        er[q] = r;
+        ec[q] = c;
+        const int gr = rb * TM + r, gc = kb * KB + c;
+        double v = 0.0;
+        if (gr < rows && gc < kdim)
+            v = contig_rows ? X[gr + (int64_t)gc * ld] : X[gc + (int64_t)gr * ld];
+        rem[q] = (gr < rows) ? ldexp(v, -expo[gr]) : 0.0;   // |rem| < 1
+    }
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const double x = rem[q] * 64.0;       // exact
+            const double d = rint(x);             // digit, |d| <= 64 (s = 0), <= 32 after
+            rem[q] = x - d;                       // exact, |rem| <= 1/2
+            const __nv_bfloat16 h = __double2bfloat16(d);   // exact: |d| <= 64
+            *reinterpret_cast<__nv_bfloat16 *>(stage + digit_off(er[q], ec[q])) = h;
+        }
+        __syncthreads();
+        uint4 *dst = reinterpret_cast<uint4 *>(
+            tiles + (((int64_t)s * row_blocks + rb) * kblocks + kb) * (TM * KB));
+        const uint4 *src = reinterpret_cast<const uint4 *>(stage);
+        for (int c = tid; c < TILE_BYTES / 16; c += 256) dst[c] = src[c];
+        __syncthreads();
+    }
+}
+
+// ---- digit-product GEMM with FP64 recombination -----------------------------------------
+
+struct Unit {
+    int s, t, chunk;
+};
+
+// Unit u of the work list: digit pairs by level l = s + t (2 .. S+1), then k-chunks.
+__device__ __forceinline__ Unit unit_of(int u, int nchunks)
+{
+    Unit x;
+    x.chunk = u % nchunks;
+    int pr = u / nchunks;
+    int l = 2;
+    while (pr >= l - 1) {
+        pr -= l - 1;
+        ++l;
+    }
+    x.s = pr + 1;
+    x.t = l - x.s;
+    return x;
+}
+
+__global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ib = blockIdx.x % p.mt, jb = blockIdx.x / p.mt;
+    const int nchunks = (p.kt + KC_BLOCKS - 1) / KC_BLOCKS;
+    const int npairs = p.slices * (p.slices + 1) / 2;
+    const int units = npairs * nchunks;
+
+    if (tid == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&sm.full[i], 1);
+            mbar_init(&sm.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sm.tfull[i], 1);
+            mbar_init(&sm.tempty[i], EPI_WARPS);
+        }
+        mbar_init(&sm.drain, 1);
+        sm.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(&sm.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int u = 0; u < units && !aborted(sm); ++u) {
+                const Unit x = unit_of(u, nchunks);
+                const int k0 = x.chunk * KC_BLOCKS;
+                const int k1 = min(p.kt, k0 + KC_BLOCKS);
+                for (int kb = k0; kb < k1; ++kb) {
+                    if (!mbar_wait(&sm.empty[stage], phase ^ 1, sm, p.status)) break;
+                    mbar_expect_tx(&sm.full[stage], 2 * TILE_BYTES);
+                    const uint16_t *ta =
+                        p.sa + (((int64_t)(x.s - 1) * p.mt + ib) * p.kt + kb) * (TM * KB);
+                    const uint16_t *tb =
+                        p.sb + (((int64_t)(x.t - 1) * p.nt + jb) * p.kt + kb) * (TN * KB);
+                    bulk_copy(sm.a[stage], ta, TILE_BYTES, &sm.full[stage]);
+                    bulk_copy(sm.b[stage], tb, TILE_BYTES, &sm.full[stage]);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int u = 0; u < units && !aborted(sm); ++u) {
+                const int buf = u & 1;
+                const uint32_t use = (uint32_t)(u >> 1);
+                if (!mbar_wait(&sm.tempty[buf], (use & 1) ^ 1, sm, p.status)) break;
+                tc_fence_after();
+                const Unit x = unit_of(u, nchunks);
+                const int k0 = x.chunk * KC_BLOCKS;
+                const int k1 = min(p.kt, k0 + KC_BLOCKS);
+                const uint32_t dcol = tmem + (uint32_t)(buf * TN);
+                bool ok = true;
+                for (int kb = k0; kb < k1; ++kb) {
+                    if (!mbar_wait(&sm.full[stage], phase, sm, p.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = saddr(sm.a[stage]), b0 = saddr(sm.b[stage]);
+#pragma unroll
+                    for (int kk = 0; kk < KB / 16; ++kk)
+                        mma_bf16(dcol, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32),
+                                 (kb > k0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&sm.empty[stage]);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&sm.tfull[buf]);
+            }
+            // all MMAs this thread issued have completed once this commit arrives
+            mma_commit(&sm.drain);
+            mbar_wait(&sm.drain, 0, sm, p.status);
+        }
+    } else {
+        // epilogue warps: TMEM lane quarter from warp % 4, column half from (warp - 2) / 4
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        const int row = ib * TM + quarter * 32 + lane;
+        double acc[64];
+#pragma unroll
+        for (int c = 0; c < 64; ++c) acc[c] = 0.0;
+        for (int u = 0; u < units; ++u) {
+            const int buf = u & 1;
+            const uint32_t use = (uint32_t)(u >> 1);
+            if (!mbar_wait(&sm.tfull[buf], use & 1, sm, p.status)) break;
+            tc_fence_after();
+            const Unit x = unit_of(u, nchunks);
+            const double scale = ldexp(1.0, -BETA_BITS * (x.s + x.t));
+            const uint32_t taddr =
+                tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * TN + half * 64);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                uint32_t r[16];
+                tmem_ld16(taddr + g * 16, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    acc[g * 16 + c] = fma((double)__uint_as_float(r[c]), scale, acc[g * 16 + c]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.tempty[buf]);
+        }
+        if (!aborted(sm) && row < p.m) {
+            const int er = p.ea[row];
+            const bool read_c = (p.beta != 0.0);
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+                const int col = jb * TN + half * 64 + c;
+                if (col < p.n) {
+                    double v = p.alpha * ldexp(acc[c], er + p.eb[col]);
+                    double *cp = p.C + row + (int64_t)col * p.ldc;
+                    if (read_c) v = fma(p.beta, *cp, v);
+                    *cp = v;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+}
+
+}  // namespace oz
+
+size_t ozaki_smem_bytes()
+{
+    return sizeof(oz::Smem) + 1024;
+}
+
+cudaError_t launch_ozaki(const OzakiParams &p, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(oz::ozaki_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(ozaki_smem_bytes()));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int rb_a = p.mt, rb_b = p.nt;
+    oz::row_exponent_kernel<<<rb_a, 256, 0, s>>>(p.A, p.lda, p.m, p.k, p.a_contig_rows, p.ea);
+    oz::row_exponent_kernel<<<rb_b, 256, 0, s>>>(p.B, p.ldb, p.n, p.k, p.b_contig_rows, p.eb);
+    oz::split_kernel<<<rb_a * p.kt, 256, 0, s>>>(p.A, p.lda, p.m, p.k, p.a_contig_rows,
+                                                 p.slices, p.ea, p.sa, rb_a, p.kt);
+    oz::split_kernel<<<rb_b * p.kt, 256, 0, s>>>(p.B, p.ldb, p.n, p.k, p.b_contig_rows,
+                                                 p.slices, p.eb, p.sb, rb_b, p.kt);
+    oz::ozaki_kernel<<<p.mt * p.nt, oz::THREADS, ozaki_smem_bytes(), s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace gfip

@@ -29,6 +29,7 @@ GFIP_ERR_ARG = 7
 GFIP_ERR_SCRATCH_LIMIT = 8
 GFIP_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 GFIP_STATUS_BAD_SEGMENT = 0x1
+GFIP_STATUS_MMA_TIMEOUT = 0x2
 
 GFIP_PACK_AUTO, GFIP_PACK_NONE, GFIP_PACK_A, GFIP_PACK_B, GFIP_PACK_BOTH = range(5)
 
@@ -55,6 +56,8 @@ SIGNATURES = {
     "gfip_error_string": (ctypes.c_char_p, [_int]),
     "gfip_dgemm_noalloc": (_int, [_chr, _chr, _i64, _i64, _i64, _dbl, _ptr, _i64, _ptr, _i64,
                                   _dbl, _ptr, _i64, _ptr]),
+    "gfip_ozaki_workspace_size": (_sz, [_ptr, _i64, _i64, _i64, _int]),
+    "gfip_dgemm_ozaki": (_int, _GEMM_D + [_int]),
 }
 
 _lock = threading.Lock()
@@ -175,6 +178,17 @@ def gfip_dgemm_noalloc(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, 
                                      B or None, ldb, beta, C or None, ldc, stream or None)
 
 
+def gfip_ozaki_workspace_size(handle, m, n, k, slices) -> int:
+    return load().gfip_ozaki_workspace_size(handle, m, n, k, slices)
+
+
+def gfip_dgemm_ozaki(handle, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                     slices) -> int:
+    """FP64 GEMM emulated with exact BF16 digit products on the tensor cores."""
+    return load().gfip_dgemm_ozaki(handle, _b(transa), _b(transb), m, n, k, alpha, A or None,
+                                   lda, B or None, ldb, beta, C or None, ldc, slices)
+
+
 ENTRY = {
     ("fused", 8): "gfip_dgemm", ("fused", 4): "gfip_sgemm",
     ("direct", 8): "gfip_dgemm_direct", ("direct", 4): "gfip_sgemm_direct",
@@ -220,6 +234,13 @@ class Handle:
             if rc != GFIP_OK:
                 raise GemmError(rc, "gfip_set_stream")
             self.stream = s.cuda_stream
+
+    def ensure_ozaki_workspace(self, m, n, k, slices):
+        need = gfip_ozaki_workspace_size(self.h, m, n, k, slices)
+        if self.workspace is None or self.workspace.numel() < need:
+            if self.workspace is not None:
+                self._torch.cuda.current_stream().synchronize()
+            self._set_ws(int(need * 1.1) + (1 << 20))
 
     def set_pack_policy(self, policy: int):
         rc = gfip_set_pack_policy(self.h, policy)
