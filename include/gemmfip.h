@@ -138,11 +138,12 @@ int gfip_sgemm_pack_then_compute(gfip_handle_t handle, char transa, char transb,
  * computed from exact BF16 digit products on the tcgen05 tensor cores (Ozaki splitting).
  * Every row of op(A) and column of op(B) is scaled by a power of two and split into `slices`
  * 6-bit integer digits (1 <= slices <= 10); the digit pairs (s, t) with s + t <= slices + 1 are
- * multiplied on the tensor cores with exact FP32 accumulation over k-chunks of 4096, and
+ * multiplied on the tensor cores with exact FP32 accumulation over k-chunks of 16384, and
  * recombined in FP64.  The result is NOT the IEEE FP64 product: its error against the exact
- * product is bounded by about k * 2^(e_i + f_j) * 2^(-6*slices) * (slices + 5) / 4 * |alpha|
- * plus FP64 rounding, where 2^e_i and 2^f_j bound the magnitudes in row i of op(A) and column
- * j of op(B); slices = 9 reaches FP64-level accuracy for data of uniform magnitude.
+ * product is bounded by about k * 2^(e_i + f_j) * 2^(-6*slices) * (slices + 2) * |alpha|
+ * plus FP64 rounding, where 2^e_i and 2^f_j are the powers of two just above the largest
+ * magnitude in row i of op(A) and column j of op(B); slices = 9 reaches FP64-level accuracy
+ * for data of uniform magnitude.
  * Same argument conventions, quick returns and error codes as gfip_dgemm, plus
  * GFIP_ERR_ARG for a slice count out of range.  Needs gfip_ozaki_workspace_size() bytes of
  * workspace.  A timeout inside the kernel raises GFIP_STATUS_MMA_TIMEOUT. */

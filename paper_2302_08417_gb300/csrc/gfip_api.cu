@@ -309,7 +309,7 @@ int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_
 // Workspace of the tensor-core FP64 emulation: digit tiles and exponents after a control
 // region of at least the header (which holds the status word).
 struct OzPlan {
-    int mt = 0, nt = 0, kt = 0;
+    int mt = 0, nt = 0, kt = 0, ks_a = 1, ks_b = 1;
     size_t off_ea = 0, off_eb = 0, off_sa = 0, off_sb = 0, data_bytes = 0;
 };
 
@@ -319,11 +319,14 @@ OzPlan oz_plan(int64_t m, int64_t n, int64_t k, int slices)
     o.mt = static_cast<int>((m + 127) / 128);
     o.nt = static_cast<int>((n + 127) / 128);
     o.kt = static_cast<int>((k + 63) / 64);
+    // enough exponent-reduction blocks to cover the GPU (about 600), at most 64 k-ranges
+    o.ks_a = std::max(1, std::min({64, o.kt, (600 + o.mt - 1) / std::max(1, o.mt)}));
+    o.ks_b = std::max(1, std::min({64, o.kt, (600 + o.nt - 1) / std::max(1, o.nt)}));
     size_t d = 0;
     o.off_ea = d;
-    d += round_up((size_t)o.mt * 128 * sizeof(int), kAlign);
+    d += round_up((size_t)o.ks_a * o.mt * 128 * sizeof(int), kAlign);
     o.off_eb = d;
-    d += round_up((size_t)o.nt * 128 * sizeof(int), kAlign);
+    d += round_up((size_t)o.ks_b * o.nt * 128 * sizeof(int), kAlign);
     o.off_sa = d;
     d += (size_t)slices * o.mt * o.kt * 16384;
     o.off_sb = d;
@@ -602,6 +605,8 @@ int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, 
     p.mt = o.mt;
     p.nt = o.nt;
     p.kt = o.kt;
+    p.ks_a = o.ks_a;
+    p.ks_b = o.ks_b;
     p.ea = reinterpret_cast<int *>(data + o.off_ea);
     p.eb = reinterpret_cast<int *>(data + o.off_eb);
     p.sa = reinterpret_cast<uint16_t *>(data + o.off_sa);

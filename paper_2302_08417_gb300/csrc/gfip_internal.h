@@ -111,8 +111,9 @@ struct OzakiParams {
     int b_contig_rows;   // 1: column j of op(B) = row j of its K-major form runs along memory ('T')
     int slices;          // digits per element (S)
     int mt, nt, kt;      // 128-row blocks of m and n, 64-wide k blocks
-    int *ea;             // [mt * 128] row exponents of op(A)
-    int *eb;             // [nt * 128] column exponents of op(B)
+    int ks_a, ks_b;      // k-ranges the exponent reductions are split into
+    int *ea;             // [ks_a][mt * 128] partial row exponents of op(A)
+    int *eb;             // [ks_b][nt * 128] partial column exponents of op(B)
     uint16_t *sa;        // [S][mt][kt] digit tiles of op(A), 16 KB each
     uint16_t *sb;        // [S][nt][kt] digit tiles of op(B)
     unsigned int *status;

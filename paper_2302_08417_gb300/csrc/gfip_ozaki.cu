@@ -7,12 +7,14 @@
 // Splitting (a pack-time transform, like the slicing that the GEMMFIP paper's future work,
 // Sec. 5, folds into packing): every row i of op(A) gets an exponent e_i with
 // max_p |a_ip| < 2^e_i, and every element becomes exactly
-//     a_ip = 2^e_i * (sum_{s=1..S} d_s * 2^(-6 s) + r),   |d_1| <= 64, |d_s| <= 32 (s > 1),
-// with integer digits d_s (exact in BF16) and |r| <= 2^(-6 S - 1).  Columns of op(B) are split
-// the same way with exponents f_j.  A product of two digits is an integer of at most 2^12, so
-// a sum of up to 4096 of them is an integer below 2^24 and the tensor cores' FP32
-// accumulation of such a k-chunk is exact.  The product is recombined in FP64:
-//     C_ij = alpha * 2^(e_i + f_j) * sum_{s+t <= S+1} 2^(-6(s+t)) * sum_chunks D_st + beta*C_ij,
+//     a_ip = 2^(e_i + 1) * (sum_{s=1..S} d_s * 2^(-6 s) + r),   |d_s| <= 32,
+// with integer digits d_s (exact in BF16) and |r| <= 2^(-6 S - 1) (the scaled element is below
+// 1/2, so even the first digit is at most 32).  Columns of op(B) are split the same way with
+// exponents f_j.  A product of two digits is an integer of at most 2^10, so a sum of up to
+// 16384 of them is an integer of at most 2^24 and the tensor cores' FP32 accumulation of such
+// a k-chunk is exact.  The product is recombined in FP64:
+//     C_ij = alpha * 2^(e_i + f_j + 2) * sum_{s+t <= S+1} 2^(-6(s+t)) * sum_chunks D_st
+//            + beta * C_ij,
 // dropping the digit pairs with s + t > S + 1 (triangular truncation).
 //
 // Kernel layout (one CTA per 128 x 128 tile of C, 10 warps):
@@ -38,11 +40,11 @@ constexpr int TM = 128;              // tile rows (M of the MMA) and digit-tile 
 constexpr int TN = 128;              // tile cols (N of the MMA)
 constexpr int KB = 64;               // k per digit tile: 64 BF16 = one 128-byte row
 constexpr int TILE_BYTES = TM * KB * 2;  // 16 KB per digit tile (A and B alike)
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;
 constexpr int THREADS = 320;
 constexpr int EPI_WARPS = 8;
 constexpr int BETA_BITS = 6;         // bits per digit
-constexpr int KC_BLOCKS = 4096 / KB; // k-blocks per exactly accumulated chunk
+constexpr int KC_BLOCKS = 16384 / KB; // k-blocks per exactly accumulated chunk
 constexpr uint32_t TMEM_COLS = 256;  // two 128-column FP32 accumulators
 constexpr unsigned STATUS_TIMEOUT = 0x2u;  // mirrors GFIP_STATUS_MMA_TIMEOUT
 constexpr long long WAIT_LIMIT = 1ll << 26;  // polls before a wait gives up
@@ -195,64 +197,119 @@ __device__ __forceinline__ uint32_t digit_off(int r, int c)
 
 // ---- splitting ---------------------------------------------------------------------------
 
-// Exponent of each row: e with max_p |x_rp| < 2^e (0 for an all-zero row).  Row r of the
-// operand has element (r, p) at X[r + p*ld] when contig_rows, else X[p + r*ld].
+// Exponent of each row: e with max_p |x_rp| < 2^e.  Block (rb, ks) covers rows
+// rb*128 .. +127 and the ks-th of KS equal k-ranges and writes the exponent of its partial
+// maximum (NO_EXP for an all-zero range) to part[ks * rows_pad + r]; row_exp() takes the
+// maximum over the KS parts (the exponent of a maximum is the maximum of the exponents).
+// Row r of the operand has element (r, p) at X[r + p*ld] when contig_rows, else X[p + r*ld].
+constexpr int NO_EXP = -(1 << 20);
+
+// |x| as an integer with the same order as the magnitudes of finite doubles.
+__device__ __forceinline__ unsigned long long mag_bits(double x)
+{
+    return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// e with |x| < 2^e for the double whose magnitude bits are b (NO_EXP for zero).
+__device__ __forceinline__ int exp_of(unsigned long long b)
+{
+    if (b == 0) return NO_EXP;
+    const int ex = static_cast<int>(b >> 52);
+    if (ex == 0) return -1074 + 64 - __clzll(static_cast<long long>(b));  // subnormal
+    return ex - 1022;   // |x| = 1.f * 2^(ex-1023) < 2^(ex-1022)
+}
+
 __global__ void __launch_bounds__(256) row_exponent_kernel(const double *X, int64_t ld,
                                                            int rows, int kdim, int contig_rows,
-                                                           int *expo)
+                                                           int row_blocks, int ks_count,
+                                                           int *part)
 {
-    __shared__ double red[256];
+    __shared__ unsigned long long red[256];
     const int tid = threadIdx.x;
-    const int r0 = blockIdx.x * TM;
-    double mx = 0.0;
+    const int rb = blockIdx.x % row_blocks, ks = blockIdx.x / row_blocks;
+    const int rows_pad = row_blocks * TM;
+    const int kr = (kdim + ks_count - 1) / ks_count;
+    const int p0 = ks * kr, p1 = min(kdim, p0 + kr);
+    const int r0 = rb * TM;
     if (contig_rows) {
         // two threads per row, consecutive rows in consecutive threads
         const int r = r0 + (tid % TM);
+        unsigned long long mx = 0;
         if (r < rows)
-            for (int p = tid / TM; p < kdim; p += 2) mx = fmax(mx, fabs(X[r + (int64_t)p * ld]));
+            for (int p = p0 + tid / TM; p < p1; p += 2) {
+                const unsigned long long b = mag_bits(X[r + (int64_t)p * ld]);
+                mx = b > mx ? b : mx;
+            }
         red[tid] = mx;
         __syncthreads();
         if (tid < TM) {
-            mx = fmax(red[tid], red[tid + TM]);
-            if (r0 + tid < rows) {
-                int e = 0;
-                if (mx > 0.0) frexp(mx, &e);   // mx = f * 2^e, 0.5 <= f < 1  =>  mx < 2^e
-                expo[r0 + tid] = e;
-            }
+            const unsigned long long a = red[tid], b = red[tid + TM];
+            part[ks * rows_pad + r0 + tid] = exp_of(a > b ? a : b);
         }
     } else {
         // one warp per row, lanes along the contiguous k
         const int lane = tid & 31, w = tid >> 5;
         for (int rr = w; rr < TM; rr += 8) {
             const int r = r0 + rr;
-            double m2 = 0.0;
+            unsigned long long m2 = 0;
             if (r < rows)
-                for (int p = lane; p < kdim; p += 32) m2 = fmax(m2, fabs(X[p + (int64_t)r * ld]));
-            for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-            if (lane == 0 && r < rows) {
-                int e = 0;
-                if (m2 > 0.0) frexp(m2, &e);
-                expo[r] = e;
+                for (int p = p0 + lane; p < p1; p += 32) {
+                    const unsigned long long b = mag_bits(X[p + (int64_t)r * ld]);
+                    m2 = b > m2 ? b : m2;
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long b = __shfl_xor_sync(0xffffffffu, m2, o);
+                m2 = b > m2 ? b : m2;
             }
+            if (lane == 0) part[ks * rows_pad + r] = exp_of(m2);
         }
     }
 }
 
-// Digit tiles of one 128 x 64 block: every element is scaled by 2^-e_row and split into S
-// base-64 digits by repeated scale-round-subtract (all steps exact in FP64).  Digit s of all
-// elements is staged in shared memory in the swizzled tile layout, then written out with
-// 16-byte stores.  Fringe rows and k positions give zero digits.
+// Row exponent from the KS partial exponents (0 for an all-zero row).
+__device__ __forceinline__ int row_exp(const int *part, int ks_count, int rows_pad, int r)
+{
+    int e = NO_EXP;
+    for (int ks = 0; ks < ks_count; ++ks) e = max(e, part[ks * rows_pad + r]);
+    return e == NO_EXP ? 0 : e;
+}
+
+// x * 2^-(e+1) as a signed fixed-point number with 63 fractional bits, truncated toward zero
+// (|x| < 2^e, so the result is below 2^62 in magnitude).  Integer operations on the IEEE bit
+// pattern only.  For an integer x the truncation drops nothing.
+__device__ __forceinline__ long long to_fixed(double x, int e)
+{
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int ex = static_cast<int>((bits >> 52) & 0x7FF);
+    long long mant = static_cast<long long>(bits & 0xFFFFFFFFFFFFFull);
+    int ee = ex;
+    if (ex == 0) ee = 1; else mant |= 1ll << 52;   // x = +-mant * 2^(ee - 1075)
+    const int sh = ee - 1075 + 62 - e;              // x * 2^(62 - e) = mant * 2^sh
+    long long v;
+    if (sh >= 0) v = mant << sh;
+    else v = (sh > -64) ? (mant >> -sh) : 0;
+    return (bits >> 63) ? -v : v;
+}
+
+// Digit tiles of one 128 x 64 block: every element is scaled by 2^-(e_row+1) (below 1/2) and
+// split into S base-64 digits by round-to-nearest on a 63-bit fixed-point copy, all in
+// integer arithmetic: d_s = round(X / 2^(63-6s)), X -= d_s * 2^(63-6s).  Digit s of all elements
+// is staged in shared memory in the swizzled tile layout, then written out with 16-byte
+// stores.  Fringe rows and k positions give zero digits.
 __global__ void __launch_bounds__(256) split_kernel(const double *X, int64_t ld, int rows,
                                                     int kdim, int contig_rows, int S,
-                                                    const int *expo, uint16_t *tiles,
-                                                    int row_blocks, int kblocks)
+                                                    const int *part, int ks_count,
+                                                    uint16_t *tiles, int row_blocks, int kblocks)
 {
     __shared__ __align__(1024) uint8_t stage[TILE_BYTES];
+    __shared__ int expo[TM];
     const int tid = threadIdx.x;
     const int rb = blockIdx.x % row_blocks, kb = blockIdx.x / row_blocks;
+    if (tid < TM) expo[tid] = row_exp(part, ks_count, row_blocks * TM, rb * TM + tid);
+    __syncthreads();
     constexpr int PER = TM * KB / 256;   // 32 elements per thread
-    double rem[PER];
-    int er[PER], ec[PER];
+    long long rem[PER];
+    uint32_t off[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         int r, c;
@@ -263,22 +320,22 @@ __global__ void __launch_bounds__(256) split_kernel(const double *X, int64_t ld,
             c = tid % KB;
             r = tid / KB + 4 * q;
         }
-        er[q] = r;
-        ec[q] = c;
+        off[q] = digit_off(r, c);
         const int gr = rb * TM + r, gc = kb * KB + c;
         double v = 0.0;
         if (gr < rows && gc < kdim)
             v = contig_rows ? X[gr + (int64_t)gc * ld] : X[gc + (int64_t)gr * ld];
-        rem[q] = (gr < rows) ? ldexp(v, -expo[gr]) : 0.0;   // |rem| < 1
+        rem[q] = (gr < rows) ? to_fixed(v, expo[r]) : 0;
     }
     for (int s = 0; s < S; ++s) {
+        const int sh = 63 - 6 * (s + 1);   // the digit's weight, >= 3 for S <= 10
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
-            const double x = rem[q] * 64.0;       // exact
-            const double d = rint(x);             // digit, |d| <= 64 (s = 0), <= 32 after
-            rem[q] = x - d;                       // exact, |rem| <= 1/2
-            const __nv_bfloat16 h = __double2bfloat16(d);   // exact: |d| <= 64
-            *reinterpret_cast<__nv_bfloat16 *>(stage + digit_off(er[q], ec[q])) = h;
+            const long long d = (rem[q] + (1ll << (sh - 1))) >> sh;   // round to nearest
+            rem[q] -= d << sh;                                       // |rem| <= 2^(sh-1)
+            // |d| <= 32: exact in BF16
+            *reinterpret_cast<__nv_bfloat16 *>(stage + off[q]) =
+                __int2bfloat16_rn(static_cast<int>(d));
         }
         __syncthreads();
         uint4 *dst = reinterpret_cast<uint4 *>(
@@ -317,7 +374,14 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
     Smem &sm = *reinterpret_cast<Smem *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ib = blockIdx.x % p.mt, jb = blockIdx.x / p.mt;
+    // CTAs that run at the same time cover a band of GROUP tile-rows, so they share digit
+    // panels of A (within the band) and of B (across it) in L2
+    constexpr int GROUP = 8;
+    const int band = blockIdx.x / (GROUP * p.nt);
+    const int in_band = blockIdx.x % (GROUP * p.nt);
+    const int rows_in_band = min(GROUP, p.mt - band * GROUP);
+    const int ib = band * GROUP + in_band % rows_in_band;
+    const int jb = in_band / rows_in_band;
     const int nchunks = (p.kt + KC_BLOCKS - 1) / KC_BLOCKS;
     const int npairs = p.slices * (p.slices + 1) / 2;
     const int units = npairs * nchunks;
@@ -439,13 +503,14 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
             if (lane == 0) mbar_arrive(&sm.tempty[buf]);
         }
         if (!aborted(sm) && row < p.m) {
-            const int er = p.ea[row];
+            const int er = row_exp(p.ea, p.ks_a, p.mt * TM, row) + 2;  // 2^(e_i+1) 2^(f_j+1)
             const bool read_c = (p.beta != 0.0);
 #pragma unroll
             for (int c = 0; c < 64; ++c) {
                 const int col = jb * TN + half * 64 + c;
                 if (col < p.n) {
-                    double v = p.alpha * ldexp(acc[c], er + p.eb[col]);
+                    double v =
+                        p.alpha * ldexp(acc[c], er + row_exp(p.eb, p.ks_b, p.nt * TN, col));
                     double *cp = p.C + row + (int64_t)col * p.ldc;
                     if (read_c) v = fma(p.beta, *cp, v);
                     *cp = v;
@@ -480,12 +545,14 @@ cudaError_t launch_ozaki(const OzakiParams &p, cudaStream_t s)
         configured = true;
     }
     const int rb_a = p.mt, rb_b = p.nt;
-    oz::row_exponent_kernel<<<rb_a, 256, 0, s>>>(p.A, p.lda, p.m, p.k, p.a_contig_rows, p.ea);
-    oz::row_exponent_kernel<<<rb_b, 256, 0, s>>>(p.B, p.ldb, p.n, p.k, p.b_contig_rows, p.eb);
+    oz::row_exponent_kernel<<<rb_a * p.ks_a, 256, 0, s>>>(p.A, p.lda, p.m, p.k, p.a_contig_rows,
+                                                           rb_a, p.ks_a, p.ea);
+    oz::row_exponent_kernel<<<rb_b * p.ks_b, 256, 0, s>>>(p.B, p.ldb, p.n, p.k, p.b_contig_rows,
+                                                           rb_b, p.ks_b, p.eb);
     oz::split_kernel<<<rb_a * p.kt, 256, 0, s>>>(p.A, p.lda, p.m, p.k, p.a_contig_rows,
-                                                 p.slices, p.ea, p.sa, rb_a, p.kt);
+                                                 p.slices, p.ea, p.ks_a, p.sa, rb_a, p.kt);
     oz::split_kernel<<<rb_b * p.kt, 256, 0, s>>>(p.B, p.ldb, p.n, p.k, p.b_contig_rows,
-                                                 p.slices, p.eb, p.sb, rb_b, p.kt);
+                                                 p.slices, p.eb, p.ks_b, p.sb, rb_b, p.kt);
     oz::ozaki_kernel<<<p.mt * p.nt, oz::THREADS, ozaki_smem_bytes(), s>>>(p);
     return cudaGetLastError();
 }
