@@ -246,6 +246,71 @@ def spectrum(h, g, torch, sizes=(16, 64, 256, 1024, 4096), reps=5):
     return out
 
 
+def emulation_report(h, g, torch, n=8192, slice_counts=(3, 5, 7, 9), samples=2048):
+    """FP64 emulated on the tensor cores (gfip_dgemm_ozaki): GFLOP/s (FP64-equivalent, 2n^3 per
+    call, device time) and the error against the oracle on sampled entries, for uniform[-1,1]
+    and log-uniform [1e-4, 1e4] magnitudes with random sign."""
+    import numpy as np
+    import oracle
+    ld = n + PAD
+    out = {"n": n, "note": "N/N, ld = n + 7, alpha 1, beta 0.5; error = max over sampled "
+           "entries of |C - C_oracle| / (|alpha||A||B| + |beta||C0|) entrywise"}
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(99)
+    for dist in ("uniform", "logmag"):
+        def mat():
+            u = torch.rand((n, ld), generator=gen, dtype=torch.float64, device="cuda")
+            if dist == "uniform":
+                return u * 2 - 1
+            mag = torch.pow(10.0, torch.rand((n, ld), generator=gen, dtype=torch.float64,
+                                             device="cuda") * 8 - 4)
+            return torch.where(u < 0.5, -mag, mag)
+        A, B, C0 = mat(), mat(), mat()
+        hA = A.cpu().numpy().reshape(-1)
+        hB = B.cpu().numpy().reshape(-1)
+        hC0 = C0.cpu().numpy().reshape(-1)
+        rng = np.random.Generator(np.random.PCG64(5))
+        ii = rng.integers(0, n, samples)
+        jj = rng.integers(0, n, samples)
+        threads = os.cpu_count() or 1
+        ref = oracle.entries("N", "N", n, n, n, 1.0, hA, ld, hB, ld, BETA, hC0, ld, ii, jj,
+                             nthreads=threads)
+        mag = oracle.entries("N", "N", n, n, n, 1.0, hA, ld, hB, ld, BETA, hC0, ld, ii, jj,
+                             absval=True, nthreads=threads)
+        rows = {}
+        for S in slice_counts:
+            h.ensure_ozaki_workspace(n, n, n, S)
+            C = C0.clone()
+
+            def call():
+                rc = g.gfip_dgemm_ozaki(h.h, "N", "N", n, n, n, 1.0, A.data_ptr(), ld,
+                                        B.data_ptr(), ld, BETA, C.data_ptr(), ld, S)
+                assert rc == 0, rc
+            C.copy_(C0)
+            call()
+            torch.cuda.synchronize()
+            got = C.cpu().numpy().reshape(-1)[ii + jj * ld]
+            err = np.abs(got - ref) / mag
+            best = float("inf")
+            for _ in range(2):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                call()
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            gf = gflop(n, n, n) / (best * 1e-3)
+            rows[f"slices_{S}"] = {"gflops": round(gf, 1),
+                                   "speedup_vs_dfma_peak": round(gf / FP64_PEAK_GFLOPS, 2),
+                                   "max_rel_err": float(f"{err.max():.3e}"),
+                                   "median_rel_err": float(f"{np.median(err):.3e}")}
+        out[dist] = rows
+        del A, B, C0
+    out["status"] = h.status()
+    return out
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -298,6 +363,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-spectrum", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-emulation", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=M, help="m = n = k (default: the headline)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
@@ -422,6 +488,8 @@ def main():
         result["cpu_baseline"] = cpu_oracle_sample(
             bufA.numpy().reshape(-1), bufB.numpy().reshape(-1), bufC.numpy().reshape(-1),
             M, K, lda, ldb, ldc)
+    if rank == 0 and not args.no_emulation:
+        result["emulated_fp64"] = emulation_report(h, g, torch)
     if rank == 0 and not args.no_spectrum:
         result["spectrum_gflops"] = spectrum(h, g, torch)
         result["spectrum_gflops"]["note"] = ("N/N, ld = m + 7, beta = 0.5, best of a few "

@@ -64,6 +64,7 @@ typedef struct gfip_handle_s *gfip_handle_t;
 /* Device status bits, reported by gfip_get_status(). */
 #define GFIP_STATUS_BAD_SEGMENT 0x1u   /* a split tile saw more partial sums than planned */
 #define GFIP_STATUS_MMA_TIMEOUT 0x2u   /* gfip_dgemm_ozaki: a pipeline wait gave up (result invalid) */
+#define GFIP_STATUS_BAD_PROBLEM 0x4u   /* grouped GEMM: a problem had invalid arguments (skipped)  */
 
 /* Pack policies for gfip_set_pack_policy(). */
 #define GFIP_PACK_AUTO 0        /* Sec. 3.3 option table: pack A iff > 1 tile column, B iff > 1 tile
@@ -152,6 +153,32 @@ size_t gfip_ozaki_workspace_size(gfip_handle_t handle, int64_t m, int64_t n, int
 int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n,
                      int64_t k, double alpha, const double *A, int64_t lda, const double *B,
                      int64_t ldb, double beta, double *C, int64_t ldc, int slices);
+
+/* ---- Grouped GEMM: many independent problems of uneven sizes in one launch ----------------
+ * The size-unified code path of Sec. 1 and Sec. 3 applied to a batch: for g < count,
+ *     C_g := alpha[g] * op(A_g) * op(B_g) + beta[g] * C_g
+ * with per-problem transa[g], transb[g] ('N','T','C'), m[g], n[g], k[g], leading dimensions and
+ * matrix pointers.  EVERY array argument is a DEVICE array of `count` entries (the pointer
+ * arrays hold device pointers), so the call reads nothing on the host and can be captured in
+ * a CUDA graph: it enqueues a preparation kernel, a prefix-sum kernel and one persistent
+ * GEMM kernel on the handle's stream.  Each problem follows the reference-BLAS rules of
+ * gfip_dgemm; a problem with invalid arguments is skipped (its C untouched) and raises
+ * GFIP_STATUS_BAD_PROBLEM.  `tile` selects the tile shape (GFIP_GROUP_TILE_*: chosen by the
+ * Python autotuner); FP64 has one tile shape.  Needs gfip_grouped_workspace_size() bytes of
+ * workspace.  Returns GFIP_ERR_ARG for count < 0 or an unknown tile. */
+#define GFIP_GROUP_TILE_DEFAULT 0   /* the single-GEMM tile (FP32 128 x 128, FP64 32 x 32)  */
+#define GFIP_GROUP_TILE_SMALL 1     /* FP32 64 x 64 tile for small problems                 */
+size_t gfip_grouped_workspace_size(gfip_handle_t handle, int count);
+int gfip_dgemm_grouped(gfip_handle_t handle, int count, const char *transa, const char *transb,
+                       const int *m, const int *n, const int *k, const double *alpha,
+                       const double *const *A, const int64_t *lda, const double *const *B,
+                       const int64_t *ldb, const double *beta, double *const *C,
+                       const int64_t *ldc, int tile);
+int gfip_sgemm_grouped(gfip_handle_t handle, int count, const char *transa, const char *transb,
+                       const int *m, const int *n, const int *k, const float *alpha,
+                       const float *const *A, const int64_t *lda, const float *const *B,
+                       const int64_t *ldb, const float *beta, float *const *C,
+                       const int64_t *ldc, int tile);
 
 /* Waits for the handle's stream, then returns the OR of the device status bits
  * (GFIP_STATUS_*) raised since the previous call of this function, and clears them.

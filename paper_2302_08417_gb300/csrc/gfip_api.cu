@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/gemmfip.h"
+#include "gfip_grouped.h"
 #include "gfip_internal.h"
 
 namespace {
@@ -544,6 +545,15 @@ const char *gfip_error_string(int code)
     }
 }
 
+size_t gfip_grouped_workspace_size(gfip_handle_t handle, int count)
+{
+    Handle *h = get(handle);
+    if (h == nullptr || count < 0) return 0;
+    const size_t desc = round_up((size_t)count * sizeof(gfip::GroupDesc<double>), kAlign);
+    const size_t pre = round_up(((size_t)count + 1) * sizeof(int), kAlign);
+    return std::max(h->ctrl_bytes, kCtrlGranule) + desc + pre;
+}
+
 size_t gfip_ozaki_workspace_size(gfip_handle_t handle, int64_t m, int64_t n, int64_t k,
                                  int slices)
 {
@@ -616,6 +626,86 @@ int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, 
     h->last_launches = 5;
     h->last_grid = o.mt * o.nt;
     return GFIP_OK;
+}
+
+}  // extern "C"
+
+
+namespace {
+
+template <typename T>
+int grouped_entry(gfip_handle_t handle, int count, const char *transa, const char *transb,
+                  const int *m, const int *n, const int *k, const T *alpha, const T *const *A,
+                  const int64_t *lda, const T *const *B, const int64_t *ldb, const T *beta,
+                  T *const *C, const int64_t *ldc, int tile)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    if (count < 0 || tile < GFIP_GROUP_TILE_DEFAULT || tile > GFIP_GROUP_TILE_SMALL)
+        return GFIP_ERR_ARG;
+    h->last_launches = 0;
+    h->last_grid = 0;
+    if (count == 0) return GFIP_OK;
+    if (!transa || !transb || !m || !n || !k || !alpha || !A || !lda || !B || !ldb || !beta ||
+        !C || !ldc)
+        return GFIP_ERR_NULLPTR;
+    if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
+    const size_t desc = round_up((size_t)count * sizeof(gfip::GroupDesc<T>), kAlign);
+    const size_t pre = round_up(((size_t)count + 1) * sizeof(int), kAlign);
+    const size_t ctrl_want = std::max(h->ctrl_bytes, kCtrlGranule);
+    if (ctrl_want + desc + pre > h->ws_bytes) return GFIP_ERR_WORKSPACE;
+    if (ctrl_want > h->ctrl_bytes) {
+        if (cudaMemsetAsync(h->ws + h->ctrl_bytes, 0, ctrl_want - h->ctrl_bytes, h->stream) !=
+            cudaSuccess)
+            return GFIP_ERR_CUDA;
+        h->ctrl_bytes = ctrl_want;
+    }
+    unsigned char *data = h->ws + h->ctrl_bytes;
+    gfip::GroupParams<T> gp{};
+    gp.count = count;
+    gp.transa = transa;
+    gp.transb = transb;
+    gp.m = m;
+    gp.n = n;
+    gp.k = k;
+    gp.alpha = alpha;
+    gp.beta = beta;
+    gp.A = A;
+    gp.B = B;
+    gp.C = C;
+    gp.lda = lda;
+    gp.ldb = ldb;
+    gp.ldc = ldc;
+    gp.desc = reinterpret_cast<gfip::GroupDesc<T> *>(data);
+    gp.prefix = reinterpret_cast<int *>(data + desc);
+    gp.status = reinterpret_cast<unsigned int *>(h->ws);
+    if (gfip::launch_grouped<T>(gp, tile, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
+    h->last_launches = 3;
+    return GFIP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gfip_dgemm_grouped(gfip_handle_t handle, int count, const char *transa, const char *transb,
+                       const int *m, const int *n, const int *k, const double *alpha,
+                       const double *const *A, const int64_t *lda, const double *const *B,
+                       const int64_t *ldb, const double *beta, double *const *C,
+                       const int64_t *ldc, int tile)
+{
+    return grouped_entry<double>(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb,
+                                 beta, C, ldc, tile);
+}
+
+int gfip_sgemm_grouped(gfip_handle_t handle, int count, const char *transa, const char *transb,
+                       const int *m, const int *n, const int *k, const float *alpha,
+                       const float *const *A, const int64_t *lda, const float *const *B,
+                       const int64_t *ldb, const float *beta, float *const *C,
+                       const int64_t *ldc, int tile)
+{
+    return grouped_entry<float>(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb,
+                                beta, C, ldc, tile);
 }
 
 }  // extern "C"

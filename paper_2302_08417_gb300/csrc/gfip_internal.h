@@ -121,6 +121,13 @@ struct OzakiParams {
 cudaError_t launch_ozaki(const OzakiParams &p, cudaStream_t s);
 size_t ozaki_smem_bytes();
 
+// Grouped GEMM (gfip_grouped.cu): many independent problems in one persistent launch.
+enum GroupTile : int { GROUP_TILE_DEFAULT = 0, GROUP_TILE_SMALL = 1 };
+template <typename T> struct GroupDesc;
+template <typename T> struct GroupParams;
+template <typename T>
+cudaError_t launch_grouped(const GroupParams<T> &gp, int tile, cudaStream_t s);
+
 // Launchers (defined per element type in gfip_f64.cu / gfip_f32.cu).
 template <typename T> cudaError_t launch_gemm(const GemmParams<T> &p, cudaStream_t s);
 template <typename T> cudaError_t launch_pack(const PackParams<T> &p, cudaStream_t s);

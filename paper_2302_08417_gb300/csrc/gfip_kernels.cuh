@@ -267,8 +267,8 @@ __device__ __forceinline__ void tile_coords(int t, int mt, int nt, int &i, int &
     j = 1 + t / (mt - 1);
 }
 
-template <typename T> struct GemmSmem {
-    using Cfg = TileCfg<T>;
+template <typename T, typename C = TileCfg<T>> struct GemmSmem {
+    using Cfg = C;
     T a[Cfg::STAGES][TileLayout<T, Cfg::BM, Cfg::BK>::ELEMS];
     T b[Cfg::STAGES][TileLayout<T, Cfg::BN, Cfg::BK>::ELEMS];
     int dec_a[2 * Cfg::STAGES];
@@ -294,8 +294,9 @@ template <> __device__ __forceinline__ void lds16<float>(float *dst, const float
     dst[3] = v.w;
 }
 
-template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
-    using Cfg = TileCfg<T>;
+template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struct Kernel {
+    using Cfg = C;
+    using Smem = GemmSmem<T, C>;
     static constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
     static constexpr int THREADS = Cfg::THREADS, STAGES = Cfg::STAGES;
     static constexpr int CH = 16 / static_cast<int>(sizeof(T));
@@ -309,6 +310,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
     static constexpr int DEC = 2 * STAGES;
     using LoadA = RawLoader<T, BM, BK, THREADS, ACONTIG>;
     using LoadB = RawLoader<T, BN, BK, THREADS, BCONTIG>;
+    using AccT = T[TM][TN];
 
     // Decision for one operand tile at one k-block, in two steps so the ready-word load
     // overlaps compute.  FIP: the first tile column produces A panels, the first tile row
@@ -335,7 +337,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
     };
 
     static __device__ __forceinline__ Words fetch_words(const GemmParams<T> &p,
-                                                        const GemmSmem<T> &sm, int i, int j,
+                                                        const Smem &sm, int i, int j,
                                                         int kb)
     {
         Words w{0ull, 0ull};
@@ -349,7 +351,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
     // Stores the decisions for local k-block q; returns true if one of them reads a tile
     // published by another CTA (the caller then issues fence_acquire()).
     static __device__ __forceinline__ bool store_decisions(const GemmParams<T> &p,
-                                                           GemmSmem<T> &sm, int i, int j,
+                                                           Smem &sm, int i, int j,
                                                            Words w, int q)
     {
         const int da = classify(p.mode_a, j == 0, sm.full_a, w.a, p.epoch);
@@ -360,7 +362,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
                (db == DEC_PACKED && p.mode_b == MODE_FIP && !sm.full_b);
     }
 
-    static __device__ __forceinline__ void issue(const GemmParams<T> &p, GemmSmem<T> &sm,
+    static __device__ __forceinline__ void issue(const GemmParams<T> &p, Smem &sm,
                                                  LoadA &la, LoadB &lb, int i, int j, int kb,
                                                  int q, int tid)
     {
@@ -415,7 +417,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
 
     // Publishes the tiles this CTA produced at local k-block it (thread 0 only).
     static __device__ __forceinline__ void publish_produced(const GemmParams<T> &p,
-                                                            const GemmSmem<T> &sm, int i, int j,
+                                                            const Smem &sm, int i, int j,
                                                             int kb0, int it)
     {
         if (sm.dec_a[it % DEC] == DEC_PRODUCE)
@@ -426,7 +428,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
 
     // Accumulates op(A)[tile rows, kb0*BK : kb1*BK] * op(B)[..., tile cols] into acc, packing
     // operand tiles on the way where this tile is a producer.
-    static __device__ void run_segment(const GemmParams<T> &p, GemmSmem<T> &sm, int i, int j,
+    static __device__ void run_segment(const GemmParams<T> &p, Smem &sm, int i, int j,
                                        int kb0, int kb1, T (&acc)[TM][TN])
     {
         const int tid = threadIdx.x;
@@ -558,7 +560,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
 
     // A split tile's partial sum: store it, count arrivals, and let the last arrival add the
     // partials of all segments in k order and write C.
-    static __device__ void fixup(const GemmParams<T> &p, GemmSmem<T> &sm, int t, int i, int j,
+    static __device__ void fixup(const GemmParams<T> &p, Smem &sm, int t, int i, int j,
                                  int g, int slot, T (&acc)[TM][TN])
     {
         const int tid = threadIdx.x;
@@ -624,7 +626,7 @@ template <typename T, bool ACONTIG, bool BCONTIG> struct Kernel {
         __syncthreads();
     }
 
-    static __device__ void run(const GemmParams<T> &p, GemmSmem<T> &sm)
+    static __device__ void run(const GemmParams<T> &p, Smem &sm)
     {
         const int g = blockIdx.x;
         T acc[TM][TN];

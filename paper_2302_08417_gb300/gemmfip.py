@@ -30,6 +30,8 @@ GFIP_ERR_SCRATCH_LIMIT = 8
 GFIP_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 GFIP_STATUS_BAD_SEGMENT = 0x1
 GFIP_STATUS_MMA_TIMEOUT = 0x2
+GFIP_STATUS_BAD_PROBLEM = 0x4
+GFIP_GROUP_TILE_DEFAULT, GFIP_GROUP_TILE_SMALL = 0, 1
 
 GFIP_PACK_AUTO, GFIP_PACK_NONE, GFIP_PACK_A, GFIP_PACK_B, GFIP_PACK_BOTH = range(5)
 
@@ -57,6 +59,9 @@ SIGNATURES = {
     "gfip_dgemm_noalloc": (_int, [_chr, _chr, _i64, _i64, _i64, _dbl, _ptr, _i64, _ptr, _i64,
                                   _dbl, _ptr, _i64, _ptr]),
     "gfip_ozaki_workspace_size": (_sz, [_ptr, _i64, _i64, _i64, _int]),
+    "gfip_grouped_workspace_size": (_sz, [_ptr, _int]),
+    "gfip_dgemm_grouped": (_int, [_ptr, _int] + [_ptr] * 13 + [_int]),
+    "gfip_sgemm_grouped": (_int, [_ptr, _int] + [_ptr] * 13 + [_int]),
     "gfip_dgemm_ozaki": (_int, _GEMM_D + [_int]),
 }
 
@@ -187,6 +192,17 @@ def gfip_dgemm_ozaki(handle, transa, transb, m, n, k, alpha, A, lda, B, ldb, bet
     """FP64 GEMM emulated with exact BF16 digit products on the tensor cores."""
     return load().gfip_dgemm_ozaki(handle, _b(transa), _b(transb), m, n, k, alpha, A or None,
                                    lda, B or None, ldb, beta, C or None, ldc, slices)
+
+
+def gfip_grouped_workspace_size(handle, count) -> int:
+    return load().gfip_grouped_workspace_size(handle, count)
+
+
+def gfip_gemm_grouped(esz, handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta,
+                      C, ldc, tile) -> int:
+    """Grouped GEMM; every array argument is a device pointer (int)."""
+    fn = load().gfip_dgemm_grouped if esz == 8 else load().gfip_sgemm_grouped
+    return fn(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tile)
 
 
 ENTRY = {
