@@ -311,6 +311,93 @@ def emulation_report(h, g, torch, n=8192, slice_counts=(3, 5, 7, 9), samples=204
     return out
 
 
+def batched_report(g, torch, count=4096, seed=11):
+    """Grouped GEMM on the batched workload: `count` problems, m, n, k log-uniform in
+    [4, 256], random operand orders, leading dimensions rows + {0..7}, FP64 and FP32.
+    Reports GFLOP/s of one grouped launch replayed from a CUDA graph (tile chosen by the
+    autotuner), against the same problems as `count` single-GEMM calls (direct variant)
+    captured in one CUDA graph and issued eagerly from Python."""
+    import numpy as np
+    from paper_2302_08417_gb300 import grouped as gr
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.exp(rng.uniform(np.log(4), np.log(256), (count, 3))).round().astype(int)
+    ta = rng.choice(["N", "T"], count)
+    tb = rng.choice(["N", "T"], count)
+    pads = rng.integers(0, 8, (count, 3))
+    out = {"problems": count, "note": "m, n, k log-uniform in [4, 256], random trans, "
+           "ld = rows + {0..7}, alpha 1, beta 0.5; CUDA events around graph replays"}
+    for dtype, tag in ((torch.float64, "f64"), (torch.float32, "f32")):
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed)
+        A, B, C = [], [], []
+        for q in range(count):
+            m, n, k = (int(x) for x in sizes[q])
+            ra, ca = (m, k) if ta[q] == "N" else (k, m)
+            rb, cb = (k, n) if tb[q] == "N" else (n, k)
+
+            def mk(rows, cols, pad):
+                ld = rows + int(pad)
+                buf = torch.rand((cols, ld), generator=gen, dtype=dtype, device="cuda")
+                return buf.t()[:rows, :]
+            A.append(mk(ra, ca, pads[q, 0]))
+            B.append(mk(rb, cb, pads[q, 1]))
+            C.append(mk(m, n, pads[q, 2]))
+        batch = gr.Batch(list(ta), list(tb), A, B, C, [1.0] * count, [BETA] * count)
+        flops = batch.flops()
+        tile = gr.autotune(batch)
+        runner = gr.GraphRunner(batch, tile)
+
+        def timed(fn, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            return best
+        grouped_ms = timed(runner.replay)
+        # baseline: one single-GEMM launch per problem, captured in a CUDA graph
+        h = g.Handle()
+        esz = 8 if dtype == torch.float64 else 4
+        entry = g.ENTRY[("direct", esz)]
+        maxw = max(g.gfip_workspace_size(h.h, ta[q], tb[q], *(int(x) for x in sizes[q]), esz)
+                   for q in range(count))
+        h._set_ws(maxw + (1 << 20))
+
+        def singles():
+            for q in range(count):
+                m, n, k = (int(x) for x in sizes[q])
+                rc = g._gemm_call(entry, h.h, ta[q], tb[q], m, n, k, 1.0, A[q].data_ptr(),
+                                  A[q].stride(1), B[q].data_ptr(), B[q].stride(1), BETA,
+                                  C[q].data_ptr(), C[q].stride(1))
+                assert rc == 0, rc
+        h.bind_stream()
+        singles()
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            h.bind_stream(s)
+            with torch.cuda.graph(graph, stream=s):
+                singles()
+        h.bind_stream()
+        singles_graph_ms = timed(graph.replay)
+        singles_eager_ms = timed(singles, reps=2)
+        out[tag] = {"tile": int(tile), "gflop_per_batch": round(flops / 1e9, 3),
+                    "grouped_graph_gflops": round(flops / 1e9 / (grouped_ms * 1e-3), 1),
+                    "singles_graph_gflops": round(flops / 1e9 / (singles_graph_ms * 1e-3), 1),
+                    "singles_eager_gflops": round(flops / 1e9 / (singles_eager_ms * 1e-3), 1),
+                    "grouped_ms": round(grouped_ms, 3),
+                    "speedup_vs_singles_graph": round(singles_graph_ms / grouped_ms, 2)}
+        del runner, graph, A, B, C, batch
+    return out
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -364,6 +451,7 @@ def main():
     ap.add_argument("--no-spectrum", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-emulation", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=M, help="m = n = k (default: the headline)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
@@ -490,6 +578,8 @@ def main():
             M, K, lda, ldb, ldc)
     if rank == 0 and not args.no_emulation:
         result["emulated_fp64"] = emulation_report(h, g, torch)
+    if rank == 0 and not args.no_batched:
+        result["batched"] = batched_report(g, torch)
     if rank == 0 and not args.no_spectrum:
         result["spectrum_gflops"] = spectrum(h, g, torch)
         result["spectrum_gflops"]["note"] = ("N/N, ld = m + 7, beta = 0.5, best of a few "

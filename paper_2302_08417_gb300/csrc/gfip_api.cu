@@ -18,7 +18,9 @@ namespace {
 
 constexpr uint32_t kMagic = 0x67666970u;  // "gfip"
 constexpr size_t kAlign = 256;
-constexpr size_t kHeader = 256;             // status word and spare
+constexpr size_t kHeader = 256;             // status word, launch counters, spare
+constexpr size_t kLaunchCountOffset = 64;   // header word: GEMM launches so far (epochs)
+constexpr size_t kDoneCountOffset = 128;    // header word: finished CTAs of the running launch
 constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
 
 struct Handle {
@@ -31,7 +33,6 @@ struct Handle {
     // Bytes at the start of the workspace that hold only control words (zeros, or words a
     // kernel of this handle tagged with an older epoch).  Data never lives below this mark.
     size_t ctrl_bytes = 0;
-    unsigned int epoch = 0;
     int pack_policy = GFIP_PACK_AUTO;
     int last_launches = 0;
     int last_grid = 0;
@@ -240,12 +241,6 @@ int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_
             return GFIP_ERR_CUDA;
         h->ctrl_bytes = ctrl_want;
     }
-    // Epoch tags make the ready words and counters of earlier calls read as "unclaimed".
-    if (h->epoch == 0xffffffffu) {
-        if (cudaMemsetAsync(h->ws, 0, h->ctrl_bytes, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
-        h->epoch = 0;
-    }
-    h->epoch += 1;
 
     unsigned char *data = h->ws + h->ctrl_bytes;
     gfip::GemmParams<T> p{};
@@ -278,7 +273,8 @@ int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_
     p.pack_b = reinterpret_cast<T *>(data + pl.data_pack_b);
     p.partial = reinterpret_cast<T *>(data + pl.data_partial);
     p.status = reinterpret_cast<unsigned int *>(h->ws);
-    p.epoch = h->epoch;
+    p.launch_count = reinterpret_cast<unsigned int *>(h->ws + kLaunchCountOffset);
+    p.done_count = reinterpret_cast<unsigned int *>(h->ws + kDoneCountOffset);
 
     int launches = 0;
     if (v == Variant::PackThenCompute) {
@@ -426,7 +422,6 @@ int gfip_set_workspace(gfip_handle_t handle, void *dev_ptr, size_t bytes)
     h->ws = reinterpret_cast<unsigned char *>(dev_ptr);
     h->ws_bytes = dev_ptr ? bytes : 0;
     h->ctrl_bytes = 0;
-    h->epoch = 0;
     return GFIP_OK;
 }
 
@@ -748,7 +743,6 @@ int noalloc_setup(NoAllocDevice &d, int dev)
     d.h.ws = reinterpret_cast<unsigned char *>(ptr);
     d.h.ws_bytes = GFIP_NOALLOC_SCRATCH_BYTES;
     d.h.ctrl_bytes = 0;
-    d.h.epoch = 0;
     d.h.pack_policy = GFIP_PACK_AUTO;
     d.ready = true;
     return GFIP_OK;

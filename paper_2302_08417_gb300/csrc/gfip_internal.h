@@ -84,7 +84,8 @@ template <typename T> struct GemmParams {
     T *pack_b;                       // [nt * kt] tiles of BN * BK elements
     T *partial;                      // [grid * 2] slots of BM * BN elements
     unsigned int *status;            // device status bits (GFIP_STATUS_*)
-    unsigned int epoch;              // tag of this call (>= 1)
+    unsigned int *launch_count;      // launches so far (the epoch of a launch is this + 1)
+    unsigned int *done_count;        // CTAs of the current launch that have finished
 };
 
 // Parameters of the pack kernel of the pack-then-compute variant.

@@ -275,6 +275,7 @@ template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     int dec_b[2 * Cfg::STAGES];
     int full_a, full_b;  // the tile's whole A (B) panel is already published
     int flag;
+    unsigned int epoch;  // this launch's tag for the ready words (launch count + 1)
 };
 
 // Loads one 16-byte chunk (CH elements) from shared memory.
@@ -354,8 +355,8 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                                                            Smem &sm, int i, int j,
                                                            Words w, int q)
     {
-        const int da = classify(p.mode_a, j == 0, sm.full_a, w.a, p.epoch);
-        const int db = classify(p.mode_b, i == 0, sm.full_b, w.b, p.epoch);
+        const int da = classify(p.mode_a, j == 0, sm.full_a, w.a, sm.epoch);
+        const int db = classify(p.mode_b, i == 0, sm.full_b, w.b, sm.epoch);
         sm.dec_a[q % DEC] = da;
         sm.dec_b[q % DEC] = db;
         return (da == DEC_PACKED && p.mode_a == MODE_FIP && !sm.full_a) ||
@@ -421,9 +422,9 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                                                             int kb0, int it)
     {
         if (sm.dec_a[it % DEC] == DEC_PRODUCE)
-            publish(p.state_a + (int64_t)i * p.kt + kb0 + it, p.epoch);
+            publish(p.state_a + (int64_t)i * p.kt + kb0 + it, sm.epoch);
         if (sm.dec_b[it % DEC] == DEC_PRODUCE)
-            publish(p.state_b + (int64_t)j * p.kt + kb0 + it, p.epoch);
+            publish(p.state_b + (int64_t)j * p.kt + kb0 + it, sm.epoch);
     }
 
     // Accumulates op(A)[tile rows, kb0*BK : kb1*BK] * op(B)[..., tile cols] into acc, packing
@@ -458,9 +459,9 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         if (tid == 0) {
             // a panel whose producer finished it whole needs no per-k-block look-ups
             const bool fa = need_word(p.mode_a, j == 0, 0) &&
-                            ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) == ready_value(p.epoch);
+                            ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) == ready_value(sm.epoch);
             const bool fb = need_word(p.mode_b, i == 0, 0) &&
-                            ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) == ready_value(p.epoch);
+                            ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) == ready_value(sm.epoch);
             sm.full_a = fa;
             sm.full_b = fb;
             Words w[STAGES];
@@ -512,9 +513,9 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             // a producer that covered its whole panel publishes the panel as complete
             if (kb0 == 0 && kb1 == p.kt) {
                 if (p.mode_a == MODE_FIP && j == 0)
-                    publish(p.state_a + (int64_t)p.mt * p.kt + i, p.epoch);
+                    publish(p.state_a + (int64_t)p.mt * p.kt + i, sm.epoch);
                 if (p.mode_b == MODE_FIP && i == 0)
-                    publish(p.state_b + (int64_t)p.nt * p.kt + j, p.epoch);
+                    publish(p.state_b + (int64_t)p.nt * p.kt + j, sm.epoch);
             }
         }
     }
@@ -580,11 +581,11 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            const unsigned long long tag = static_cast<unsigned long long>(p.epoch) << 32;
+            const unsigned long long tag = static_cast<unsigned long long>(sm.epoch) << 32;
             atomicMax(p.tile_count + t, tag);
             const unsigned long long old = atomicAdd(p.tile_count + t, 1ull);
             const long long cnt = static_cast<long long>(old - tag) + 1;
-            if ((old >> 32) != p.epoch || cnt > nseg) atomicOr(p.status, STATUS_BAD_SEGMENT);
+            if ((old >> 32) != sm.epoch || cnt > nseg) atomicOr(p.status, STATUS_BAD_SEGMENT);
             sm.flag = (cnt == nseg);
             __threadfence();
         }
@@ -663,13 +664,29 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
     }
 };
 
+// The launch's epoch tags every ready word and arrival counter it writes, so words left by
+// earlier launches read as stale and nothing is cleared between calls.  It lives on the
+// device: every CTA reads the launch counter at start (epoch = counter + 1), and the last CTA
+// to finish stores the new value.  A launch replayed from a CUDA graph therefore gets a fresh
+// epoch too.  (The next launch on the stream starts only after this one has finished.)
 template <typename T, bool ACONTIG, bool BCONTIG>
 __global__ void __launch_bounds__(TileCfg<T>::THREADS, TileCfg<T>::MIN_BLOCKS)
     gemm_kernel(const GemmParams<T> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     GemmSmem<T> &sm = *reinterpret_cast<GemmSmem<T> *>(smem_raw);
+    if (threadIdx.x == 0) sm.epoch = *(volatile unsigned int *)p.launch_count + 1u;
+    __syncthreads();
     Kernel<T, ACONTIG, BCONTIG>::run(p, sm);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(p.done_count, 1u) == gridDim.x - 1) {
+            *(volatile unsigned int *)p.done_count = 0u;
+            *(volatile unsigned int *)p.launch_count = sm.epoch;
+            __threadfence();
+        }
+    }
 }
 
 // One (panel, k-block) tile of the pack-then-compute variant: raw load into shared memory,
