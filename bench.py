@@ -246,6 +246,104 @@ def spectrum(h, g, torch, sizes=(16, 64, 256, 1024, 4096), reps=5):
     return out
 
 
+def sweep(h, g, torch, sizes, dtypes=("f64", "f32"), target_ms=2.0):
+    """The fused-vs-plain size spectrum, N/N, ld = m + 7, alpha 1, beta 0.5, uniform[-1, 1].
+
+    For every size, dtype and variant two times per call are taken: `dev_us`, the device time
+    of R back-to-back calls captured in one CUDA graph (replayed, best of 3, divided by R), and
+    `call_us`, R eager calls from Python between two events (host overhead included).  R is 1
+    when one call takes more than half a millisecond.  Operands of the sizes below about 2048
+    stay in L2 between calls (warm), as they would in a loop of calls."""
+    import math
+    out = {"note": "N/N, ld = m + 7, alpha 1, beta 0.5, uniform[-1,1]; dev_us from CUDA-graph "
+                   "replays of R calls, call_us from R eager calls; GFLOP/s from dev_us"}
+    for tag in dtypes:
+        dtype = torch.float64 if tag == "f64" else torch.float32
+        esz = 8 if tag == "f64" else 4
+        peak = FP64_PEAK_GFLOPS if tag == "f64" else FP32_PEAK_GFLOPS
+        rows = {}
+        for n in sizes:
+            A, B, C = make_operands(n, dtype, n, n, n)
+            ld = n + PAD
+            h.ensure_workspace("N", "N", n, n, n, esz)
+            row = {}
+            for var in ("fused", "direct", "pack_then_compute"):
+                name = g.ENTRY[(var, esz)]
+
+                def call():
+                    rc = g._gemm_call(name, h.h, "N", "N", n, n, n, ALPHA, A.data_ptr(), ld,
+                                      B.data_ptr(), ld, BETA, C.data_ptr(), ld)
+                    if rc != 0:
+                        raise g.GemmError(rc, name)
+
+                def events_ms(fn, reps):
+                    best = float("inf")
+                    for _ in range(reps):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        fn()
+                        e1.record()
+                        e1.synchronize()
+                        best = min(best, e0.elapsed_time(e1))
+                    return best
+                call()
+                torch.cuda.synchronize()
+                one = events_ms(call, 1)
+                if one > 0.5:
+                    extra = 0 if one > 2000 else (1 if one > 500 else 2)
+                    dev = min(one, events_ms(call, extra)) if extra else one
+                    reps_per, call_ms, dev_ms = 1, dev, dev
+                else:
+                    R = max(1, min(400, math.ceil(target_ms / max(one, 1e-3))))
+
+                    def burst():
+                        for _ in range(R):
+                            call()
+                    call_ms = events_ms(burst, 2) / R
+                    stream = torch.cuda.Stream()
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.stream(stream):
+                        h.bind_stream(stream)
+                        with torch.cuda.graph(graph, stream=stream):
+                            burst()
+                    h.bind_stream()
+                    graph.replay()
+                    torch.cuda.synchronize()
+                    dev_ms = events_ms(graph.replay, 3) / R
+                    reps_per = R
+                    del graph
+                gf = gflop(n, n, n) / (dev_ms * 1e-3)
+                row[var] = {"gflops": round(gf, 2), "dev_us": round(dev_ms * 1e3, 2),
+                            "call_us": round(call_ms * 1e3, 2), "R": reps_per,
+                            "frac": round(gf / peak, 4)}
+            best_plain = max(row["direct"]["gflops"], row["pack_then_compute"]["gflops"])
+            row["fused_over_best_plain"] = round(row["fused"]["gflops"] / best_plain, 4)
+            rows[str(n)] = row
+            del A, B, C
+            torch.cuda.empty_cache()
+        out[tag] = rows
+    out["status"] = h.status()
+    return out
+
+
+def sweep_markdown(res) -> str:
+    lines = []
+    for tag in ("f64", "f32"):
+        if tag not in res:
+            continue
+        lines.append(f"| {tag} n | fused GF/s | direct GF/s | pack-then-compute GF/s | "
+                     "fused / best plain | fused frac of peak | fused dev us | fused call us |")
+        lines.append("|---|---|---|---|---|---|---|---|")
+        for n, r in res[tag].items():
+            lines.append(f"| {n} | {r['fused']['gflops']} | {r['direct']['gflops']} | "
+                         f"{r['pack_then_compute']['gflops']} | {r['fused_over_best_plain']} | "
+                         f"{r['fused']['frac']} | {r['fused']['dev_us']} | "
+                         f"{r['fused']['call_us']} |")
+        lines.append("")
+    return "\n".join(lines)
+
+
 def emulation_report(h, g, torch, n=8192, slice_counts=(3, 5, 7, 9), samples=2048):
     """FP64 emulated on the tensor cores (gfip_dgemm_ozaki): GFLOP/s (FP64-equivalent, 2n^3 per
     call, device time) and the error against the oracle on sampled entries, for uniform[-1,1]
@@ -457,6 +555,11 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--variant", default="fused", choices=["fused", "direct",
                                                           "pack_then_compute"])
+    ap.add_argument("--sweep", default=None, metavar="SIZES",
+                    help="only run the fused-vs-plain size sweep: 'all' (16 .. 16384) or a "
+                         "comma-separated list of sizes; prints one JSON line")
+    ap.add_argument("--sweep-dtypes", default="f64,f32")
+    ap.add_argument("--sweep-md", default=None, help="also write the sweep as a markdown table")
     args = ap.parse_args()
     if args.size != M or args.dtype != "f64" or args.variant != "fused":
         M = N = K = args.size
@@ -480,6 +583,20 @@ def main():
     h = g.Handle()
     h.bind_stream()
     stream = torch.cuda.current_stream()
+    if args.sweep is not None:
+        from paper_2302_08417_gb300 import inputs
+        sizes = (inputs.config_sizes() if args.sweep == "all"
+                 else [int(x) for x in args.sweep.split(",")])
+        clocks = ClockSampler(local)
+        clocks.start()
+        res = sweep(h, g, torch, sizes, tuple(args.sweep_dtypes.split(",")))
+        res["clocks"] = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"sweep": res}), flush=True)
+            if args.sweep_md:
+                with open(args.sweep_md, "w") as f:
+                    f.write(sweep_markdown(res))
+        return
     f64 = args.dtype == "f64"
     esz = 8 if f64 else 4
     A, B, C = make_operands(1234 + rank, torch.float64 if f64 else torch.float32)

@@ -24,7 +24,7 @@ constexpr unsigned int STATUS_BAD_PROBLEM = 0x4u;  // mirrors GFIP_STATUS_BAD_PR
 
 // FP32 tile for small problems: 64 x 64 x 32 on 64 threads (8 x 8 per thread).
 struct TileCfgF32Small {
-    static constexpr int BM = 64, BN = 64, BK = 32, THREADS = 64, NCN = 2, STAGES = 3;
+    static constexpr int BM = 64, BN = 64, BK = 32, THREADS = 64, NCM = 2, NCN = 2, STAGES = 3;
     static constexpr int MIN_BLOCKS = 4, UNROLL = 8;
 };
 
@@ -118,7 +118,7 @@ __device__ __forceinline__ void grouped_tile(const GroupDesc<T> &d, GemmSmem<T, 
     p.mode_a = MODE_RAW;
     p.mode_b = MODE_RAW;
     typename K::AccT acc;
-    K::run_segment(p, sm, i, j, 0, d.kt, acc);
+    K::run_segment(p, sm, i, j, 0, d.kt, acc, 0u);
     K::epilogue(p, i, j, acc);
 }
 

@@ -4,11 +4,11 @@
 // operands.  Three properties carry the paper's method onto the GPU:
 //
 //  * Packed layout = shared-memory image (Sec. 2.1, Fig. 2).  An operand tile (BX x BK of
-//    op(A) or op(B)) lives in shared memory in a swizzled layout: 128-byte row segments along
-//    x, one per k, whose 16-byte chunks are XOR-permuted by (k mod 8).  The packed copy of a
-//    tile in global memory is byte-for-byte that image, so a CTA fetches a packed tile with
-//    contiguous 16-byte copies and no address arithmetic, and fringes are zero-padded once,
-//    when packing (Sec. 2.2).
+//    op(A) or op(B)) is cut into 128-byte row segments along x, one row per k.  In shared
+//    memory the rows sit at a pitch of 128 bytes plus 4 elements (bank-conflict-free raw loads
+//    and fragment reads); the packed copy in global memory holds the same rows back to back,
+//    so a CTA fetches a packed tile with contiguous 16-byte copies and no per-element address
+//    arithmetic, and fringes are zero-padded once, when packing (Sec. 2.2).
 //
 //  * Fused-in packing (Sec. 3.1 Alg. 1, Sec. 3.2).  Tiles are ordered producers first: the
 //    tiles of the first tile column come first and pack the A panels, then the rest of the
@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "gfip_internal.h"
 
@@ -275,7 +276,6 @@ template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     int dec_b[2 * Cfg::STAGES];
     int full_a, full_b;  // the tile's whole A (B) panel is already published
     int flag;
-    unsigned int epoch;  // this launch's tag for the ready words (launch count + 1)
 };
 
 // Loads one 16-byte chunk (CH elements) from shared memory.
@@ -301,13 +301,14 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
     static constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
     static constexpr int THREADS = Cfg::THREADS, STAGES = Cfg::STAGES;
     static constexpr int CH = 16 / static_cast<int>(sizeof(T));
-    // register micro-tile: NCM (NCN) 16-byte chunks along m (n), the second chunk half a tile
-    // away from the first
-    static constexpr int NCM = 2, NCN = Cfg::NCN;
+    // register micro-tile: NCM (NCN) 16-byte chunks along m (n), chunk c at c/NCM (c/NCN)
+    // of the tile
+    static constexpr int NCM = Cfg::NCM, NCN = Cfg::NCN;
     static constexpr int TM = NCM * CH, TN = NCN * CH;
     static constexpr int TX = BM / TM;               // threads along m
     static_assert(TX * (BN / TN) == THREADS, "thread grid must cover the tile");
     static_assert(NCN == 1 || NCN == 2, "one or two chunks along n");
+    static_assert(NCM == 2 || NCM == 4, "two or four chunks along m");
     static constexpr int DEC = 2 * STAGES;
     using LoadA = RawLoader<T, BM, BK, THREADS, ACONTIG>;
     using LoadB = RawLoader<T, BN, BK, THREADS, BCONTIG>;
@@ -353,10 +354,10 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
     // published by another CTA (the caller then issues fence_acquire()).
     static __device__ __forceinline__ bool store_decisions(const GemmParams<T> &p,
                                                            Smem &sm, int i, int j,
-                                                           Words w, int q)
+                                                           Words w, int q, unsigned int epoch)
     {
-        const int da = classify(p.mode_a, j == 0, sm.full_a, w.a, sm.epoch);
-        const int db = classify(p.mode_b, i == 0, sm.full_b, w.b, sm.epoch);
+        const int da = classify(p.mode_a, j == 0, sm.full_a, w.a, epoch);
+        const int db = classify(p.mode_b, i == 0, sm.full_b, w.b, epoch);
         sm.dec_a[q % DEC] = da;
         sm.dec_b[q % DEC] = db;
         return (da == DEC_PACKED && p.mode_a == MODE_FIP && !sm.full_a) ||
@@ -395,42 +396,84 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         using LA = TileLayout<T, BM, BK>;
         using LB = TileLayout<T, BN, BK>;
         const T *a0 = As + LA::off(tx * CH, 0);
-        const T *a1 = As + LA::off(BM / 2 + tx * CH, 0);
         const T *b0 = Bs + LB::off(ty * CH, 0);
-        const T *b1 = Bs + LB::off((NCN == 2 ? BN / 2 : 0) + ty * CH, 0);
+        // chunk c of a fragment sits c * BM / NCM (BN / NCN) further along x: whole 128-byte
+        // segments, i.e. a constant offset in the layout
+        static_assert((BM / NCM) % LA::W == 0 && (NCN == 1 || (BN / NCN) % LB::W == 0),
+                      "fragment chunks must be whole segments apart");
+        constexpr int DA = (BM / NCM) / LA::W * LA::SEG, DB = (BN / NCN) / LB::W * LB::SEG;
 #pragma unroll 1
         for (int k0 = 0; k0 < BK; k0 += UNROLL) {
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 const int kk = k0 + u;
                 T a[TM], b[TN];
-                lds16<T>(a, a0 + kk * LA::P);
-                lds16<T>(a + CH, a1 + kk * LA::P);
-                lds16<T>(b, b0 + kk * LB::P);
-                if (NCN == 2) lds16<T>(b + CH, b1 + kk * LB::P);
 #pragma unroll
-                for (int ii = 0; ii < TM; ++ii)
+                for (int c = 0; c < NCM; ++c)
+                    lds16<T>(a + c * CH, a0 + c * DA + kk * LA::P);
 #pragma unroll
-                    for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fma(a[ii], b[jj], acc[ii][jj]);
+                for (int c = 0; c < NCN; ++c)
+                    lds16<T>(b + c * CH, b0 + c * DB + kk * LB::P);
+                fma_block(a, b, acc);
             }
+        }
+    }
+
+    // acc[ii][jj] += a[ii] * b[jj].  FP32 uses the paired FMA of sm_100+ (two lanes of
+    // independent single-rounding FMAs per instruction, so the result bits equal fmaf's),
+    // which halves the instructions the FFMA-bound loop issues.
+    static __device__ __forceinline__ void fma_block(const T (&a)[TM], const T (&b)[TN],
+                                                     T (&acc)[TM][TN])
+    {
+        if constexpr (std::is_same<T, float>::value && TM >= TN) {
+            // pairs along m: {a[ii], a[ii+1]} x b[jj] (b[jj] duplicated once per jj)
+#pragma unroll
+            for (int jj = 0; jj < TN; ++jj) {
+                const float2 bb = make_float2(b[jj], b[jj]);
+#pragma unroll
+                for (int ii = 0; ii < TM; ii += 2) {
+                    const float2 c = __ffma2_rn(make_float2(a[ii], a[ii + 1]), bb,
+                                                make_float2(acc[ii][jj], acc[ii + 1][jj]));
+                    acc[ii][jj] = c.x;
+                    acc[ii + 1][jj] = c.y;
+                }
+            }
+        } else if constexpr (std::is_same<T, float>::value) {
+            // pairs along n: a[ii] x {b[jj], b[jj+1]}
+#pragma unroll
+            for (int ii = 0; ii < TM; ++ii) {
+                const float2 aa = make_float2(a[ii], a[ii]);
+#pragma unroll
+                for (int jj = 0; jj < TN; jj += 2) {
+                    const float2 c = __ffma2_rn(aa, make_float2(b[jj], b[jj + 1]),
+                                                make_float2(acc[ii][jj], acc[ii][jj + 1]));
+                    acc[ii][jj] = c.x;
+                    acc[ii][jj + 1] = c.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fma(a[ii], b[jj], acc[ii][jj]);
         }
     }
 
     // Publishes the tiles this CTA produced at local k-block it (thread 0 only).
     static __device__ __forceinline__ void publish_produced(const GemmParams<T> &p,
                                                             const Smem &sm, int i, int j,
-                                                            int kb0, int it)
+                                                            int kb0, int it, unsigned int epoch)
     {
         if (sm.dec_a[it % DEC] == DEC_PRODUCE)
-            publish(p.state_a + (int64_t)i * p.kt + kb0 + it, sm.epoch);
+            publish(p.state_a + (int64_t)i * p.kt + kb0 + it, epoch);
         if (sm.dec_b[it % DEC] == DEC_PRODUCE)
-            publish(p.state_b + (int64_t)j * p.kt + kb0 + it, sm.epoch);
+            publish(p.state_b + (int64_t)j * p.kt + kb0 + it, epoch);
     }
 
     // Accumulates op(A)[tile rows, kb0*BK : kb1*BK] * op(B)[..., tile cols] into acc, packing
     // operand tiles on the way where this tile is a producer.
     static __device__ void run_segment(const GemmParams<T> &p, Smem &sm, int i, int j,
-                                       int kb0, int kb1, T (&acc)[TM][TN])
+                                       int kb0, int kb1, T (&acc)[TM][TN], unsigned int epoch)
     {
         const int tid = threadIdx.x;
         const int tx = tid % TX, ty = tid / TX;
@@ -459,9 +502,9 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         if (tid == 0) {
             // a panel whose producer finished it whole needs no per-k-block look-ups
             const bool fa = need_word(p.mode_a, j == 0, 0) &&
-                            ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) == ready_value(sm.epoch);
+                            ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) == ready_value(epoch);
             const bool fb = need_word(p.mode_b, i == 0, 0) &&
-                            ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) == ready_value(sm.epoch);
+                            ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) == ready_value(epoch);
             sm.full_a = fa;
             sm.full_b = fb;
             Words w[STAGES];
@@ -471,7 +514,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             bool acq = fa || fb;
 #pragma unroll
             for (int q = 0; q < STAGES; ++q)
-                if (q < nkb) acq |= store_decisions(p, sm, i, j, w[q], q);
+                if (q < nkb) acq |= store_decisions(p, sm, i, j, w[q], q, epoch);
             if (acq) fence_acquire();
         }
         __syncthreads();
@@ -500,22 +543,22 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             if (ahead) w = fetch_words(p, sm, i, j, kb0 + it + STAGES);
             compute(sm.a[stage], sm.b[stage], acc, tx, ty);
             if (tid == 0) {
-                if (ahead && store_decisions(p, sm, i, j, w, it + STAGES)) fence_acquire();
+                if (ahead && store_decisions(p, sm, i, j, w, it + STAGES, epoch)) fence_acquire();
                 // the pack stores of the previous k-block were ordered by this iteration's
                 // barrier and have drained during the compute
-                if (it > 0) publish_produced(p, sm, i, j, kb0, it - 1);
+                if (it > 0) publish_produced(p, sm, i, j, kb0, it - 1, epoch);
             }
         }
         cp_async_wait<0>();
         __syncthreads();
         if (tid == 0 && nkb > 0) {
-            publish_produced(p, sm, i, j, kb0, nkb - 1);
+            publish_produced(p, sm, i, j, kb0, nkb - 1, epoch);
             // a producer that covered its whole panel publishes the panel as complete
             if (kb0 == 0 && kb1 == p.kt) {
                 if (p.mode_a == MODE_FIP && j == 0)
-                    publish(p.state_a + (int64_t)p.mt * p.kt + i, sm.epoch);
+                    publish(p.state_a + (int64_t)p.mt * p.kt + i, epoch);
                 if (p.mode_b == MODE_FIP && i == 0)
-                    publish(p.state_b + (int64_t)p.nt * p.kt + j, sm.epoch);
+                    publish(p.state_b + (int64_t)p.nt * p.kt + j, epoch);
             }
         }
     }
@@ -539,12 +582,12 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             T c[TM];
 #pragma unroll
             for (int ii = 0; ii < TM; ++ii) {
-                const int row = m0 + tx * CH + (ii % CH) + (ii / CH) * (BM / 2);
+                const int row = m0 + tx * CH + (ii % CH) + (ii / CH) * (BM / NCM);
                 c[ii] = (read_c && row < p.m) ? ccol[row] : T(0);
             }
 #pragma unroll
             for (int ii = 0; ii < TM; ++ii) {
-                const int row = m0 + tx * CH + (ii % CH) + (ii / CH) * (BM / 2);
+                const int row = m0 + tx * CH + (ii % CH) + (ii / CH) * (BM / NCM);
                 if (row >= p.m) continue;
                 T v = p.alpha * acc[ii][jj];
                 if (read_c) v = fma(p.beta, c[ii], v);
@@ -562,7 +605,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
     // A split tile's partial sum: store it, count arrivals, and let the last arrival add the
     // partials of all segments in k order and write C.
     static __device__ void fixup(const GemmParams<T> &p, Smem &sm, int t, int i, int j,
-                                 int g, int slot, T (&acc)[TM][TN])
+                                 int g, int slot, T (&acc)[TM][TN], unsigned int epoch)
     {
         const int tid = threadIdx.x;
         const int64_t S = p.sk_iters;
@@ -581,11 +624,11 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            const unsigned long long tag = static_cast<unsigned long long>(sm.epoch) << 32;
+            const unsigned long long tag = static_cast<unsigned long long>(epoch) << 32;
             atomicMax(p.tile_count + t, tag);
             const unsigned long long old = atomicAdd(p.tile_count + t, 1ull);
             const long long cnt = static_cast<long long>(old - tag) + 1;
-            if ((old >> 32) != sm.epoch || cnt > nseg) atomicOr(p.status, STATUS_BAD_SEGMENT);
+            if ((old >> 32) != epoch || cnt > nseg) atomicOr(p.status, STATUS_BAD_SEGMENT);
             sm.flag = (cnt == nseg);
             __threadfence();
         }
@@ -627,14 +670,16 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         __syncthreads();
     }
 
-    static __device__ void run(const GemmParams<T> &p, Smem &sm)
+    // Thread 0's `epoch` tags the ready words and arrival counters this launch writes (only
+    // thread 0 of a CTA reads or writes them).
+    static __device__ void run(const GemmParams<T> &p, Smem &sm, unsigned int epoch)
     {
         const int g = blockIdx.x;
         T acc[TM][TN];
         for (int t = g; t < p.dp_tiles; t += p.grid) {
             int i, j;
             tile_coords(t, p.mt, p.nt, i, j);
-            run_segment(p, sm, i, j, 0, p.kt, acc);
+            run_segment(p, sm, i, j, 0, p.kt, acc, epoch);
             epilogue(p, i, j, acc);
             __syncthreads();
         }
@@ -651,12 +696,12 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                 const int64_t rest = hi - q;
                 const int kb1 =
                     (rest < (int64_t)(p.kt - kb0)) ? kb0 + static_cast<int>(rest) : p.kt;
-                run_segment(p, sm, i, j, kb0, kb1, acc);
+                run_segment(p, sm, i, j, kb0, kb1, acc, epoch);
                 if (kb0 == 0 && kb1 == p.kt) {
                     epilogue(p, i, j, acc);
                     __syncthreads();
                 } else {
-                    fixup(p, sm, t, i, j, g, (u == first_u) ? 0 : 1, acc);
+                    fixup(p, sm, t, i, j, g, (u == first_u) ? 0 : 1, acc, epoch);
                 }
                 q += kb1 - kb0;
             }
@@ -666,24 +711,25 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
 
 // The launch's epoch tags every ready word and arrival counter it writes, so words left by
 // earlier launches read as stale and nothing is cleared between calls.  It lives on the
-// device: every CTA reads the launch counter at start (epoch = counter + 1), and the last CTA
-// to finish stores the new value.  A launch replayed from a CUDA graph therefore gets a fresh
-// epoch too.  (The next launch on the stream starts only after this one has finished.)
+// device: thread 0 of every CTA reads the launch counter at start (epoch = counter + 1), and
+// the last CTA to finish stores the new value, so a launch replayed from a CUDA graph gets a
+// fresh epoch too.  (The next launch on the stream starts only after this one has finished,
+// and every CTA has read the counter before it counts itself finished.)  The counter is held
+// in a register: only thread 0 uses it, so its load latency hides behind the first loads.
 template <typename T, bool ACONTIG, bool BCONTIG>
 __global__ void __launch_bounds__(TileCfg<T>::THREADS, TileCfg<T>::MIN_BLOCKS)
     gemm_kernel(const GemmParams<T> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     GemmSmem<T> &sm = *reinterpret_cast<GemmSmem<T> *>(smem_raw);
-    if (threadIdx.x == 0) sm.epoch = *(volatile unsigned int *)p.launch_count + 1u;
-    __syncthreads();
-    Kernel<T, ACONTIG, BCONTIG>::run(p, sm);
-    __syncthreads();
+    unsigned int epoch = 0u;
+    if (threadIdx.x == 0) epoch = *(volatile unsigned int *)p.launch_count + 1u;
+    Kernel<T, ACONTIG, BCONTIG>::run(p, sm, epoch);
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(p.done_count, 1u) == gridDim.x - 1) {
             *(volatile unsigned int *)p.done_count = 0u;
-            *(volatile unsigned int *)p.launch_count = sm.epoch;
+            *(volatile unsigned int *)p.launch_count = epoch;
             __threadfence();
         }
     }
