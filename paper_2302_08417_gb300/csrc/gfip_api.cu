@@ -22,6 +22,7 @@ constexpr size_t kHeader = 256;             // status word, launch counters, spa
 constexpr size_t kLaunchCountOffset = 64;   // header word: GEMM launches so far (epochs)
 constexpr size_t kDoneCountOffset = 128;    // header word: finished CTAs of the running launch
 constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
+constexpr int kMinSplitRun = 8;              // shortest k run per CTA in a split wave
 
 struct Handle {
     uint32_t magic = kMagic;
@@ -123,8 +124,12 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
         pl.dp_tiles = 0;
         pl.sk_iters = total_iters;
     } else {
+        // The partial last wave is split along k.  If that would give each CTA a short run
+        // (fewer than kMinSplitRun k-blocks, where the fix-up would dominate), one full wave
+        // more is split with it.
         const int rem = pl.tiles % full;
-        const int sk_tiles = rem + full;
+        const bool short_run = (int64_t)rem * pl.kt < (int64_t)kMinSplitRun * full;
+        const int sk_tiles = short_run ? rem + full : rem;
         pl.grid = full;
         pl.dp_tiles = pl.tiles - sk_tiles;
         pl.sk_iters = (int64_t)sk_tiles * pl.kt;
@@ -157,9 +162,10 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
         default: {
             // AUTO: Sec. 3.3's table (an A panel is reused only across tile columns, a B
             // panel only across tile rows), read for a GPU: a packed copy pays off only for
-            // tiles that run after its producer, i.e. when there are more tiles than one wave
-            // of CTAs; tiles running side by side with the producer read the raw operand
-            const bool later = pl.tiles > pl.grid;
+            // tiles that run after its producer, i.e. when a whole data-parallel wave (which
+            // holds the producers) runs before other tiles; tiles running side by side with
+            // the producer read the raw operand
+            const bool later = pl.tiles > pl.grid && pl.dp_tiles >= pl.grid;
             pl.mode_a = (pl.nt > 1 && later) ? gfip::MODE_FIP : gfip::MODE_RAW;
             pl.mode_b = (pl.mt > 1 && later) ? gfip::MODE_FIP : gfip::MODE_RAW;
             break;
