@@ -43,10 +43,10 @@ HBM_GBS = 6785.2
 WORKLOAD = ("fp64 gemm m=n=k=8192 N/N lda=ldb=ldc=8199 alpha=1 beta=0.5 uniform[-1,1] "
             "fused-in-packing")
 
-# DRAM traffic of one launch of the FP64 GEMM kernel on this workload, from an ncu capture
-# of a smaller case scaled by tiles processed (see profiles/); valid only while the kernel
-# sources hash to KERNEL_HASH.
-TRAFFIC = {"bytes_per_launch": None, "kernel_hash": None}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the FP64 GEMM
+# kernel on this workload, from a one-pass ncu capture of the full-size launch (summary in
+# profiles/); valid only while the kernel sources hash to kernel_hash.
+TRAFFIC = {"bytes_per_launch": 35.44e9 + 1.66e9, "kernel_hash": "af4061f147a77d9a"}
 KERNEL_SOURCES = ["paper_2302_08417_gb300/csrc/gfip_kernels.cuh",
                   "paper_2302_08417_gb300/csrc/gfip_internal.h"]
 
@@ -560,6 +560,11 @@ def main():
                          "comma-separated list of sizes; prints one JSON line")
     ap.add_argument("--sweep-dtypes", default="f64,f32")
     ap.add_argument("--sweep-md", default=None, help="also write the sweep as a markdown table")
+    ap.add_argument("--emulation-only", type=int, default=0, metavar="N",
+                    help="only run the emulated-FP64 report at m = n = k = N")
+    ap.add_argument("--slices", default="3,5,7,9", help="digit counts of the emulated report")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="COUNT",
+                    help="only run the grouped-GEMM report on COUNT problems")
     args = ap.parse_args()
     if args.size != M or args.dtype != "f64" or args.variant != "fused":
         M = N = K = args.size
@@ -583,6 +588,17 @@ def main():
     h = g.Handle()
     h.bind_stream()
     stream = torch.cuda.current_stream()
+    if args.emulation_only or args.batched_only:
+        out = {}
+        if args.emulation_only:
+            out["emulated_fp64"] = emulation_report(
+                h, g, torch, n=args.emulation_only,
+                slice_counts=tuple(int(x) for x in args.slices.split(",")))
+        if args.batched_only:
+            out["batched"] = batched_report(g, torch, count=args.batched_only)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     if args.sweep is not None:
         from paper_2302_08417_gb300 import inputs
         sizes = (inputs.config_sizes() if args.sweep == "all"
@@ -694,7 +710,8 @@ def main():
             bufA.numpy().reshape(-1), bufB.numpy().reshape(-1), bufC.numpy().reshape(-1),
             M, K, lda, ldb, ldc)
     if rank == 0 and not args.no_emulation:
-        result["emulated_fp64"] = emulation_report(h, g, torch)
+        result["emulated_fp64"] = emulation_report(
+            h, g, torch, slice_counts=tuple(int(x) for x in args.slices.split(",")))
     if rank == 0 and not args.no_batched:
         result["batched"] = batched_report(g, torch)
     if rank == 0 and not args.no_spectrum:

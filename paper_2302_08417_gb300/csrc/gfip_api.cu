@@ -2,6 +2,7 @@
 // codes), quick returns, the launch plan (tile grid, schedule, pack modes), the workspace
 // layout, and the launches.  See include/gemmfip.h for the contract.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <limits>
@@ -267,6 +268,9 @@ int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_
     p.nt = pl.nt;
     p.kt = pl.kt;
     p.tiles = pl.tiles;
+    // consumer bands of about sqrt(grid) tile rows: a wave spans ~sqrt(grid) panels each way
+    p.band = std::max(1, std::min(pl.mt - 1, static_cast<int>(std::lround(std::sqrt(
+                                                 static_cast<double>(pl.grid))))));
     p.grid = pl.grid;
     p.dp_tiles = pl.dp_tiles;
     p.sk_iters = pl.sk_iters;

@@ -82,6 +82,7 @@ template <typename T> struct GemmParams {
     int b_contig_n;   // 1: op(B)[p,j] = B[j + p*ldb] (transb 'T'); 0: B[p + j*ldb]
     int mt, nt, kt;   // tile counts along m, n and k
     int tiles;        // mt * nt
+    int band;         // tile rows per band of the consumer tile order (>= 1)
     int grid;         // persistent CTAs
     int dp_tiles;     // tiles [0, dp_tiles) are data-parallel: tile t runs on CTA t % grid
     int64_t sk_iters; // (tiles - dp_tiles) * kt iterations split evenly over the CTAs

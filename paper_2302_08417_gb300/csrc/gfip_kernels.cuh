@@ -248,9 +248,11 @@ __device__ __forceinline__ void publish(unsigned long long *word, unsigned int e
 }
 
 // Tile order, producers first: t < mt are (t, 0) (first tile column, packs A), the next
-// nt - 1 are (0, j) (rest of the first tile row, packs B), then the remaining
-// (mt-1) x (nt-1) tiles in column-major order.
-__device__ __forceinline__ void tile_coords(int t, int mt, int nt, int &i, int &j)
+// nt - 1 are (0, j) (rest of the first tile row, packs B), then the (mt-1) x (nt-1) others
+// in bands of `band` tile rows, column-major within a band.  A wave of G concurrent tiles then
+// spans about band A panels and G / band B panels (band ~ sqrt(G)), which stay in L2 while
+// the wave runs, instead of every A panel of the matrix.
+__device__ __forceinline__ void tile_coords(int t, int mt, int nt, int band, int &i, int &j)
 {
     if (t < mt) {
         i = t;
@@ -264,8 +266,12 @@ __device__ __forceinline__ void tile_coords(int t, int mt, int nt, int &i, int &
         return;
     }
     t -= nt - 1;
-    i = 1 + t % (mt - 1);
-    j = 1 + t / (mt - 1);
+    const int rows = mt - 1, cols = nt - 1;
+    const int b = t / (band * cols);          // band index
+    const int h = min(band, rows - b * band);  // rows in this band (the last may be short)
+    const int r = t - b * band * cols;
+    i = 1 + b * band + r % h;
+    j = 1 + r / h;
 }
 
 template <typename T, typename C = TileCfg<T>> struct GemmSmem {
@@ -678,7 +684,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         T acc[TM][TN];
         for (int t = g; t < p.dp_tiles; t += p.grid) {
             int i, j;
-            tile_coords(t, p.mt, p.nt, i, j);
+            tile_coords(t, p.mt, p.nt, p.band, i, j);
             run_segment(p, sm, i, j, 0, p.kt, acc, epoch);
             epilogue(p, i, j, acc);
             __syncthreads();
@@ -691,7 +697,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                 const int u = static_cast<int>(q / p.kt);
                 const int t = p.dp_tiles + u;
                 int i, j;
-                tile_coords(t, p.mt, p.nt, i, j);
+                tile_coords(t, p.mt, p.nt, p.band, i, j);
                 const int kb0 = static_cast<int>(q % p.kt);
                 const int64_t rest = hi - q;
                 const int kb1 =
