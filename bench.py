@@ -496,6 +496,114 @@ def batched_report(g, torch, count=4096, seed=11):
     return out
 
 
+def autograd_report(torch, shapes=((4096, 4096, 1024), (1024, 8192, 4096)), count=1024,
+                    seed=13):
+    """Differentiable GEMM, forward + backward (three products, 6mnk flop) per step: the
+    fused kernel through autograd.gemm, the direct variant, and torch.matmul (cuBLAS, TF32
+    off) for context, at the two single shapes (N/N); then a batch of `count` uneven problems
+    (m, n, k log-uniform in [8, 128], random trans) as three grouped launches
+    (autograd.grouped_gemm) against one autograd.gemm call per problem.  Device time, CUDA
+    events, best of 3 after a warm-up."""
+    import numpy as np
+    from paper_2302_08417_gb300 import autograd as ag
+    torch.backends.cuda.matmul.allow_tf32 = False
+
+    def best_ms(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    out = {"note": "forward + backward = 3 GEMMs (6mnk flop); device time, best of 3"}
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    for dtype, tag in ((torch.float64, "f64"), (torch.float32, "f32")):
+        rows = {}
+        for m, n, k in shapes:
+            At = (torch.rand((k, m), generator=gen, dtype=dtype, device="cuda") * 2 - 1)
+            Bt = (torch.rand((n, k), generator=gen, dtype=dtype, device="cuda") * 2 - 1)
+            At.requires_grad_()
+            Bt.requires_grad_()
+            dC = torch.rand((n, m), generator=gen, dtype=dtype, device="cuda").t() * 2 - 1
+            flop = 6.0 * m * n * k
+
+            def step(kind):
+                def run():
+                    At.grad = None
+                    Bt.grad = None
+                    if kind == "cublas":
+                        C = At.t() @ Bt.t()
+                    else:
+                        C = ag.gemm(At.t(), Bt.t(), "N", "N", 1.0, kind)
+                    C.backward(dC)
+                return run
+            r = {kind: round(flop / 1e9 / (best_ms(step(kind)) * 1e-3), 1)
+                 for kind in ("fused", "direct", "cublas")}
+            r["fused_over_cublas"] = round(r["fused"] / r["cublas"], 3)
+            rows[f"{m}x{n}x{k}"] = r
+            del At, Bt, dC
+        # the uneven batch
+        rng = np.random.Generator(np.random.PCG64(seed))
+        sizes = np.exp(rng.uniform(np.log(8), np.log(128), (count, 3))).round().astype(int)
+        ta = [str(x) for x in rng.choice(["N", "T"], count)]
+        tb = [str(x) for x in rng.choice(["N", "T"], count)]
+        As, Bs = [], []
+        for q in range(count):
+            m, n, k = (int(x) for x in sizes[q])
+            ra, ca = (m, k) if ta[q] == "N" else (k, m)
+            rb, cb = (k, n) if tb[q] == "N" else (n, k)
+            As.append(torch.rand((ca, ra), generator=gen, dtype=dtype, device="cuda")
+                      .requires_grad_())
+            Bs.append(torch.rand((cb, rb), generator=gen, dtype=dtype, device="cuda")
+                      .requires_grad_())
+        dCs = [torch.rand((int(s[1]), int(s[0])), generator=gen, dtype=dtype,
+                          device="cuda").t() for s in sizes]
+        flop = float(sum(6.0 * int(s[0]) * int(s[1]) * int(s[2]) for s in sizes))
+
+        def grouped_step():
+            Cs = ag.grouped_gemm([a.t() for a in As], [b.t() for b in Bs], ta, tb, 1.0)
+            torch.autograd.backward(Cs, dCs)
+
+        def singles_step():
+            Cs = [ag.gemm(a.t(), b.t(), x, y, 1.0) for a, b, x, y in zip(As, Bs, ta, tb)]
+            torch.autograd.backward(Cs, dCs)
+        grouped_step()   # tunes the tiles once
+        g_ms = best_ms(grouped_step)
+        s_ms = best_ms(singles_step, reps=2)
+        # device time of the three grouped passes alone: each launch captured in a CUDA graph
+        from paper_2302_08417_gb300 import grouped as gr
+        At_ = [a.detach().t() for a in As]
+        Bt_ = [b.detach().t() for b in Bs]
+        passes = [ag.forward_batch(At_, Bt_, ta, tb), ag.grad_a_batch(At_, Bt_, dCs, ta, tb),
+                  ag.grad_b_batch(At_, Bt_, dCs, ta, tb)]
+        runners = []
+        for ops_a, ops_b, xa, xb, outs in passes:
+            batch = gr.Batch(ops_a, ops_b, xa, xb, outs, [1.0] * count, [0.0] * count)
+            runners.append(gr.GraphRunner(batch, gr.autotune(batch)))
+        d_ms = best_ms(lambda: [r.replay() for r in runners])
+        rows[f"batch{count}"] = {
+            "step_gflops": round(flop / 1e9 / (g_ms * 1e-3), 1),
+            "singles_step_gflops": round(flop / 1e9 / (s_ms * 1e-3), 1),
+            "step_ms": round(g_ms, 3), "singles_step_ms": round(s_ms, 3),
+            "speedup_vs_singles": round(s_ms / g_ms, 2),
+            "grouped_device_ms": round(d_ms, 3),
+            "grouped_device_gflops": round(flop / 1e9 / (d_ms * 1e-3), 1),
+            "note": "step = eager autograd forward + backward from Python (host-bound at "
+                    "this size); device = the three grouped launches replayed from graphs"}
+        del runners, passes
+        del As, Bs, dCs
+        out[tag] = rows
+    return out
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -565,6 +673,9 @@ def main():
     ap.add_argument("--slices", default="3,5,7,9", help="digit counts of the emulated report")
     ap.add_argument("--batched-only", type=int, default=0, metavar="COUNT",
                     help="only run the grouped-GEMM report on COUNT problems")
+    ap.add_argument("--autograd-only", action="store_true",
+                    help="only run the differentiable-GEMM report")
+    ap.add_argument("--no-autograd", action="store_true")
     args = ap.parse_args()
     if args.size != M or args.dtype != "f64" or args.variant != "fused":
         M = N = K = args.size
@@ -588,8 +699,10 @@ def main():
     h = g.Handle()
     h.bind_stream()
     stream = torch.cuda.current_stream()
-    if args.emulation_only or args.batched_only:
+    if args.emulation_only or args.batched_only or args.autograd_only:
         out = {}
+        if args.autograd_only:
+            out["autograd"] = autograd_report(torch)
         if args.emulation_only:
             out["emulated_fp64"] = emulation_report(
                 h, g, torch, n=args.emulation_only,
@@ -714,6 +827,8 @@ def main():
             h, g, torch, slice_counts=tuple(int(x) for x in args.slices.split(",")))
     if rank == 0 and not args.no_batched:
         result["batched"] = batched_report(g, torch)
+    if rank == 0 and not args.no_autograd:
+        result["autograd"] = autograd_report(torch)
     if rank == 0 and not args.no_spectrum:
         result["spectrum_gflops"] = spectrum(h, g, torch)
         result["spectrum_gflops"]["note"] = ("N/N, ld = m + 7, beta = 0.5, best of a few "

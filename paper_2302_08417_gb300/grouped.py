@@ -46,6 +46,8 @@ class Batch:
         self.sizes = list(zip(ms, ns, ks))
 
         def ld(x):
+            if x.dim() == 2 and x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+                return x.stride(1)
             return g._colmajor_ld(x, "matrix")
 
         i32 = dict(dtype=torch.int32, device=dev)
@@ -95,6 +97,19 @@ def run(batch: Batch, tile: int, handle: g.Handle | None = None) -> None:
         raise g.GemmError(rc, "gfip_gemm_grouped")
 
 
+def run_batch(transa, transb, A, B, C, alpha, tile=None, beta=0.0,
+              handle: g.Handle | None = None) -> Batch:
+    """C_g := alpha op(A_g) op(B_g) + beta C_g for lists of column-major tensors, as one
+    grouped launch; ``tile`` None asks :func:`autotune` (which, with beta == 0, may overwrite
+    C while timing).  Returns the batch (it keeps the operands alive)."""
+    count = len(A)
+    batch = Batch(transa, transb, A, B, C, [alpha] * count, [beta] * count)
+    if tile is None:
+        tile = autotune(batch, handle) if beta == 0.0 else TILES[batch.esz][0]
+    run(batch, tile, handle)
+    return batch
+
+
 _tuned: dict = {}
 
 
@@ -124,11 +139,14 @@ def autotune(batch: Batch, handle: g.Handle | None = None, reps: int = 3) -> int
 
 
 class GraphRunner:
-    """The grouped call of one batch captured in a CUDA graph; replay() re-runs it."""
+    """The grouped call of one batch captured in a CUDA graph; replay() re-runs it.
+
+    The captured launches point into the handle's workspace, so the runner owns a handle of
+    its own by default (a shared handle must not grow its workspace while the graph lives)."""
 
     def __init__(self, batch: Batch, tile: int, handle: g.Handle | None = None):
         self.batch = batch
-        self.handle = handle or g.default_handle()
+        self.handle = handle or g.Handle()
         run(batch, tile, self.handle)          # sizes the workspace before capture
         torch.cuda.synchronize()
         self.stream = torch.cuda.Stream()

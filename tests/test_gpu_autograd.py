@@ -145,3 +145,68 @@ def test_config_shapes_sampled(dev, dtype, m, n, k):
                          absval=True, nthreads=8)
     got = Bt.grad.t().detach().double().cpu().numpy()[ii, jj]
     assert np.all(np.abs(got - want) <= 2 * m * u * bnd)
+
+
+def _uneven_batch(seed, count, lo, hi, dtype, dev):
+    """count problems, m, n, k log-uniform in [lo, hi], random trans; stored operands are
+    leaves (their transposes are the column-major matrices passed to the GEMM)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    probs = []
+    for _ in range(count):
+        m, n, k = (int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))))) for _ in range(3))
+        ta, tb = str(rng.choice(["N", "T"])), str(rng.choice(["N", "T"]))
+        ra, ca = (m, k) if ta == "N" else (k, m)
+        rb, cb = (k, n) if tb == "N" else (n, k)
+        At = stored(ra, ca, dtype, dev, gen).requires_grad_()
+        Bt = stored(rb, cb, dtype, dev, gen).requires_grad_()
+        probs.append((m, n, k, ta, tb, At, Bt))
+    return probs
+
+
+def test_grouped_gradcheck_fp64(dev):
+    probs = _uneven_batch(41, 4, 3, 12, torch.float64, dev)
+    ta = [p[3] for p in probs]
+    tb = [p[4] for p in probs]
+    leaves = [p[5] for p in probs] + [p[6] for p in probs]
+
+    def f(*xs):
+        As, Bs = xs[:len(probs)], xs[len(probs):]
+        return tuple(ag.grouped_gemm([a.t() for a in As], [b.t() for b in Bs], ta, tb, -0.75,
+                                     tile=0))
+    assert torch.autograd.gradcheck(f, tuple(leaves), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+def test_grouped_gradients_match_oracle(dev, dtype):
+    """A batch of uneven problems (m, n, k log-uniform in [8, 128], random trans): forward
+    and both gradients of every problem against the oracle."""
+    probs = _uneven_batch(43, 96, 8, 128, dtype, dev)
+    alpha = 1.25
+    Cs = ag.grouped_gemm([p[5].t() for p in probs], [p[6].t() for p in probs],
+                         [p[3] for p in probs], [p[4] for p in probs], alpha)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(44)
+    dCs = [torch.rand(C.shape, generator=gen, dtype=dtype, device=dev) * 2 - 1 for C in Cs]
+    torch.autograd.backward(Cs, dCs)
+    u = inputs.unit_roundoff(np.float64 if dtype == torch.float64 else np.float32)
+    for (m, n, k, ta, tb, At, Bt), C, dC in zip(probs, Cs, dCs):
+        # forward
+        A, lda = _np_colmajor(At.t())
+        B, ldb = _np_colmajor(Bt.t())
+        z = np.zeros(m * n)
+        want = oracle.gemm_result(ta, tb, m, n, k, alpha, A, lda, B, ldb, 0.0, z, m)
+        bound = oracle.abs_bound(ta, tb, m, n, k, alpha, A, lda, B, ldb, 0.0, z, m)
+        got = C.detach().double().cpu().numpy()
+        assert np.all(np.abs(got - inputs.as_matrix(want, m, n, m))
+                      <= 2 * max(k, 2) * u * bound)   # abs_bound is already m x n
+        # gradients
+        ref = _ref_grads(At, Bt, dC, ta, tb, alpha, m, n, k)
+        for name, grad in (("A", At.grad.t()), ("B", Bt.grad.t())):
+            want, bound, rows, cols, inner = ref[name]
+            got = grad.detach().double().cpu().numpy()
+            want = inputs.as_matrix(want, rows, cols, rows)
+            assert got.shape == want.shape == bound.shape
+            assert np.all(np.abs(got - want) <= 2 * max(inner, 2) * u * bound), (
+                name, m, n, k, ta, tb)
