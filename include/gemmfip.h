@@ -154,6 +154,16 @@ int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, 
                      int64_t k, double alpha, const double *A, int64_t lda, const double *B,
                      int64_t ldb, double beta, double *C, int64_t ldc, int slices);
 
+/* Test hook for the failure path of gfip_dgemm_ozaki (no counterpart in the paper; the
+ * paper's CPU kernels have no waits).  Sets, for this handle's later gfip_dgemm_ozaki calls,
+ * the budget of every pipeline wait in nanoseconds (0 restores the default, 2 s), and with
+ * enable != 0 makes the first CTA withhold its first operand copy, so that its wait runs out:
+ * the call then raises GFIP_STATUS_MMA_TIMEOUT, leaves that CTA's 128 x 128 tile of C
+ * unwritten (every other tile is computed), waits for its own copies in flight, releases its
+ * tensor memory and returns; the context stays usable.  Nothing else is affected.
+ * Returns GFIP_ERR_HANDLE for an invalid handle. */
+int gfip_debug_ozaki_timeout(gfip_handle_t handle, int enable, uint64_t wait_ns);
+
 /* ---- Grouped GEMM: many independent problems of uneven sizes in one launch ----------------
  * The size-unified code path of Sec. 1 and Sec. 3 applied to a batch: for g < count,
  *     C_g := alpha[g] * op(A_g) * op(B_g) + beta[g] * C_g

@@ -23,6 +23,9 @@ LIB_SOURCES = ["gfip_api.cu", "gfip_f64.cu", "gfip_f32.cu", "gfip_ozaki.cu", "gf
 HEADERS = ["gfip_internal.h", "gfip_kernels.cuh", "gfip_grouped.h"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-I" + os.path.join(ROOT, "include")]
+# Extra nvcc arguments (e.g. "-DGFIP_F32_UNROLL=16" to override a tile parameter of
+# gfip_internal.h); a build with them is forced, since the sources did not change.
+EXTRA_FLAGS = os.environ.get("GFIP_NVCC_EXTRA", "").split()
 
 
 def nvcc() -> str:
@@ -48,6 +51,7 @@ def _run(cmd: list[str]) -> None:
 def build(force: bool = False, probe: bool = True, verbose: bool = False) -> str:
     """Compile (if stale) and return the path of libgemmfip.so."""
     os.makedirs(OUT, exist_ok=True)
+    force = force or bool(EXTRA_FLAGS)
     cc = nvcc()
     headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include",
                                                                        "gemmfip.h")]
@@ -59,7 +63,7 @@ def build(force: bool = False, probe: bool = True, verbose: bool = False) -> str
         objs.append(o)
         if force or _stale(o, [s] + headers):
             extra = ["-Xptxas", "-v"] if verbose else []
-            jobs.append([cc] + NVCC_FLAGS + extra + ["-c", s, "-o", o])
+            jobs.append([cc] + NVCC_FLAGS + EXTRA_FLAGS + extra + ["-c", s, "-o", o])
     if probe:
         ps = os.path.join(CSRC, "peak_probe.cu")
         if force or _stale(PROBE, [ps]):

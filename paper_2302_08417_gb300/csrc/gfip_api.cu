@@ -24,6 +24,7 @@ constexpr size_t kLaunchCountOffset = 64;   // header word: GEMM launches so far
 constexpr size_t kDoneCountOffset = 128;    // header word: finished CTAs of the running launch
 constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
 constexpr int kMinSplitRun = 8;              // shortest k run per CTA in a split wave
+constexpr unsigned long long kOzakiWaitNs = 2000000000ull;  // 2 s per pipeline wait
 
 struct Handle {
     uint32_t magic = kMagic;
@@ -36,6 +37,8 @@ struct Handle {
     // kernel of this handle tagged with an older epoch).  Data never lives below this mark.
     size_t ctrl_bytes = 0;
     int pack_policy = GFIP_PACK_AUTO;
+    unsigned long long oz_wait_ns = kOzakiWaitNs;  // budget of the emulation kernel's waits
+    int oz_inject = 0;                             // test hook (gfip_debug_ozaki_timeout)
     int last_launches = 0;
     int last_grid = 0;
     int bps_f64 = 0;
@@ -435,6 +438,15 @@ int gfip_set_workspace(gfip_handle_t handle, void *dev_ptr, size_t bytes)
     return GFIP_OK;
 }
 
+int gfip_debug_ozaki_timeout(gfip_handle_t handle, int enable, uint64_t wait_ns)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    h->oz_inject = enable ? 1 : 0;
+    h->oz_wait_ns = wait_ns ? wait_ns : kOzakiWaitNs;
+    return GFIP_OK;
+}
+
 int gfip_set_pack_policy(gfip_handle_t handle, int policy)
 {
     Handle *h = get(handle);
@@ -627,6 +639,8 @@ int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, 
     p.sa = reinterpret_cast<uint16_t *>(data + o.off_sa);
     p.sb = reinterpret_cast<uint16_t *>(data + o.off_sb);
     p.status = reinterpret_cast<unsigned int *>(h->ws);
+    p.wait_ns = h->oz_wait_ns;
+    p.inject_timeout = h->oz_inject;
     if (gfip::launch_ozaki(p, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
     h->last_launches = 5;
     h->last_grid = o.mt * o.nt;

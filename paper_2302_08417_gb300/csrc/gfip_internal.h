@@ -63,10 +63,13 @@ template <> struct TileCfg<double> {
 // micro-tile, reading (8 + 8) x 4 bytes per 64 FMAs, sits at the shared-memory limit; 16 x 8
 // (NCM = 4, 128 threads) reads 0.75 B/FMA and measured 4 % faster at 8192 but 5-10 % slower
 // at 1024-2048, where only 8 warps per SM are left to hide latency.
+#ifndef GFIP_F32_UNROLL
+#define GFIP_F32_UNROLL 16
+#endif
 template <> struct TileCfg<float> {
     static constexpr int BM = 128, BN = 128, BK = GFIP_F32_BK, NCM = GFIP_F32_NCM, NCN = 2;
     static constexpr int THREADS = BM * BN / (NCM * 4 * NCN * 4);
-    static constexpr int UNROLL = 8;
+    static constexpr int UNROLL = GFIP_F32_UNROLL;
     static constexpr int STAGES = GFIP_F32_STAGES, MIN_BLOCKS = GFIP_F32_MIN_BLOCKS;
 };
 
@@ -129,6 +132,8 @@ struct OzakiParams {
     uint16_t *sa;        // [S][mt][kt] digit tiles of op(A), 16 KB each
     uint16_t *sb;        // [S][nt][kt] digit tiles of op(B)
     unsigned int *status;
+    unsigned long long wait_ns;  // budget of every mbarrier wait (nanoseconds)
+    int inject_timeout;  // test hook: CTA 0 withholds its first operand copy
 };
 cudaError_t launch_ozaki(const OzakiParams &p, cudaStream_t s);
 size_t ozaki_smem_bytes();

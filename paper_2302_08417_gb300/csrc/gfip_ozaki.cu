@@ -19,13 +19,14 @@
 //
 // Kernel layout (one CTA per 128 x 128 tile of C, 10 warps):
 //   warp 0      producer: bulk-copies the A- and B-digit tiles (16 KB each, stored already in
-//               the swizzled shared-memory layout the MMA reads) into a 4-stage ring;
+//               the swizzled shared-memory layout the MMA reads) into a 6-stage ring;
 //   warp 1      allocates tensor memory and issues tcgen05.mma (one thread) into one of two
 //               128-column FP32 accumulators, one accumulator per (digit pair, k-chunk);
 //   warps 2-9   drain a finished accumulator with tcgen05.ld and add it, scaled, into FP64
 //               registers (64 values per thread), then write C.
-// Every mbarrier wait is bounded; on a timeout the kernel raises a status bit, the roles
-// skip their remaining work, and tensor memory is released before exit.
+// Every mbarrier wait is bounded by a global-timer budget; on a timeout the kernel raises a
+// status bit, the roles skip their remaining work, the producer waits for its copies in
+// flight, and tensor memory is released before exit.
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -47,7 +48,7 @@ constexpr int BETA_BITS = 6;         // bits per digit
 constexpr int KC_BLOCKS = 16384 / KB; // k-blocks per exactly accumulated chunk
 constexpr uint32_t TMEM_COLS = 256;  // two 128-column FP32 accumulators
 constexpr unsigned STATUS_TIMEOUT = 0x2u;  // mirrors GFIP_STATUS_MMA_TIMEOUT
-constexpr long long WAIT_LIMIT = 1ll << 26;  // polls before a wait gives up
+constexpr long long WAIT_POLLS = 1ll << 32;  // backstop on polls, should the timer stall
 
 struct Smem {
     uint8_t a[STAGES][TILE_BYTES];   // 1024-byte aligned (swizzle atoms)
@@ -89,25 +90,54 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
 
-// Waits for the phase with the given parity to complete; gives up after WAIT_LIMIT polls or
-// when another role has aborted.  Returns false if it gave up.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for the phase with the given parity to complete; gives up after budget_ns of the
+// global timer, or when another role has aborted.  Returns false if it gave up; a timeout
+// sets the CTA's abort flag and the status bit.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Smem &sm,
-                                          unsigned *status)
+                                          unsigned *status, unsigned long long budget_ns)
 {
     const uint32_t a = saddr(bar);
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < WAIT_POLLS; ++it) {
+        if (mbar_try(a, parity)) return true;
         if (aborted(sm)) return false;
+        if ((it & 63) == 63 && global_ns() - t0 > budget_ns) break;
     }
     *(volatile int *)&sm.abort = 1;
     atomicOr(status, STATUS_TIMEOUT);
+    return false;
+}
+
+// The same wait, used while draining after an abort: ignores the abort flag and raises
+// nothing; returns false if the budget ran out.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity,
+                                                unsigned long long budget_ns)
+{
+    const uint32_t a = saddr(bar);
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < WAIT_POLLS; ++it) {
+        if (mbar_try(a, parity)) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > budget_ns) break;
+    }
     return false;
 }
 
@@ -415,24 +445,46 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
+            long long issued = 0;   // stages handed to the copy engine (or withheld)
+            const bool withhold = p.inject_timeout && blockIdx.x == 0;
             for (int u = 0; u < units && !aborted(sm); ++u) {
                 const Unit x = unit_of(u, nchunks);
                 const int k0 = x.chunk * KC_BLOCKS;
                 const int k1 = min(p.kt, k0 + KC_BLOCKS);
+                bool ok = true;
                 for (int kb = k0; kb < k1; ++kb) {
-                    if (!mbar_wait(&sm.empty[stage], phase ^ 1, sm, p.status)) break;
-                    mbar_expect_tx(&sm.full[stage], 2 * TILE_BYTES);
-                    const uint16_t *ta =
-                        p.sa + (((int64_t)(x.s - 1) * p.mt + ib) * p.kt + kb) * (TM * KB);
-                    const uint16_t *tb =
-                        p.sb + (((int64_t)(x.t - 1) * p.nt + jb) * p.kt + kb) * (TN * KB);
-                    bulk_copy(sm.a[stage], ta, TILE_BYTES, &sm.full[stage]);
-                    bulk_copy(sm.b[stage], tb, TILE_BYTES, &sm.full[stage]);
+                    if (!mbar_wait(&sm.empty[stage], phase ^ 1, sm, p.status, p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    if (!(withhold && issued == 0)) {
+                        mbar_expect_tx(&sm.full[stage], 2 * TILE_BYTES);
+                        const uint16_t *ta =
+                            p.sa + (((int64_t)(x.s - 1) * p.mt + ib) * p.kt + kb) * (TM * KB);
+                        const uint16_t *tb =
+                            p.sb + (((int64_t)(x.t - 1) * p.nt + jb) * p.kt + kb) * (TN * KB);
+                        bulk_copy(sm.a[stage], ta, TILE_BYTES, &sm.full[stage]);
+                        bulk_copy(sm.b[stage], tb, TILE_BYTES, &sm.full[stage]);
+                    }
+                    ++issued;
                     if (++stage == STAGES) {
                         stage = 0;
                         phase ^= 1;
                     }
                 }
+                if (!ok) break;
+            }
+            // No bulk copy may still be writing shared memory when the CTA exits: wait for
+            // the last STAGES stages handed out (each is in the phase it was issued in; one
+            // the consumer already took has completed that phase).  The withheld stage, if
+            // any, has nothing in flight.
+            for (int d = 1; d <= STAGES && d <= issued; ++d) {
+                if (--stage < 0) {
+                    stage = STAGES - 1;
+                    phase ^= 1;
+                }
+                if (withhold && issued - d == 0) continue;
+                mbar_wait_drain(&sm.full[stage], phase, p.wait_ns);
             }
         }
     } else if (warp == 1) {
@@ -442,7 +494,7 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
             for (int u = 0; u < units && !aborted(sm); ++u) {
                 const int buf = u & 1;
                 const uint32_t use = (uint32_t)(u >> 1);
-                if (!mbar_wait(&sm.tempty[buf], (use & 1) ^ 1, sm, p.status)) break;
+                if (!mbar_wait(&sm.tempty[buf], (use & 1) ^ 1, sm, p.status, p.wait_ns)) break;
                 tc_fence_after();
                 const Unit x = unit_of(u, nchunks);
                 const int k0 = x.chunk * KC_BLOCKS;
@@ -450,7 +502,7 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
                 const uint32_t dcol = tmem + (uint32_t)(buf * TN);
                 bool ok = true;
                 for (int kb = k0; kb < k1; ++kb) {
-                    if (!mbar_wait(&sm.full[stage], phase, sm, p.status)) {
+                    if (!mbar_wait(&sm.full[stage], phase, sm, p.status, p.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -471,7 +523,7 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
             }
             // all MMAs this thread issued have completed once this commit arrives
             mma_commit(&sm.drain);
-            mbar_wait(&sm.drain, 0, sm, p.status);
+            mbar_wait_drain(&sm.drain, 0, p.wait_ns);
         }
     } else {
         // epilogue warps: TMEM lane quarter from warp % 4, column half from (warp - 2) / 4
@@ -483,7 +535,7 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
         for (int u = 0; u < units; ++u) {
             const int buf = u & 1;
             const uint32_t use = (uint32_t)(u >> 1);
-            if (!mbar_wait(&sm.tfull[buf], use & 1, sm, p.status)) break;
+            if (!mbar_wait(&sm.tfull[buf], use & 1, sm, p.status, p.wait_ns)) break;
             tc_fence_after();
             const Unit x = unit_of(u, nchunks);
             const double scale = ldexp(1.0, -BETA_BITS * (x.s + x.t));

@@ -63,6 +63,7 @@ SIGNATURES = {
     "gfip_dgemm_grouped": (_int, [_ptr, _int] + [_ptr] * 13 + [_int]),
     "gfip_sgemm_grouped": (_int, [_ptr, _int] + [_ptr] * 13 + [_int]),
     "gfip_dgemm_ozaki": (_int, _GEMM_D + [_int]),
+    "gfip_debug_ozaki_timeout": (_int, [_ptr, _int, ctypes.c_uint64]),
 }
 
 _lock = threading.Lock()
@@ -192,6 +193,12 @@ def gfip_dgemm_ozaki(handle, transa, transb, m, n, k, alpha, A, lda, B, ldb, bet
     """FP64 GEMM emulated with exact BF16 digit products on the tensor cores."""
     return load().gfip_dgemm_ozaki(handle, _b(transa), _b(transb), m, n, k, alpha, A or None,
                                    lda, B or None, ldb, beta, C or None, ldc, slices)
+
+
+def gfip_debug_ozaki_timeout(handle, enable: bool, wait_ns: int = 0) -> int:
+    """Test hook: later gfip_dgemm_ozaki calls withhold one operand copy in the first CTA so
+    that its bounded wait (wait_ns; 0 = the 2 s default) runs out."""
+    return load().gfip_debug_ozaki_timeout(handle, int(bool(enable)), int(wait_ns))
 
 
 def gfip_grouped_workspace_size(handle, count) -> int:

@@ -128,3 +128,41 @@ def test_bad_slice_count_rejected(runner):
     for s in (0, 11):
         rc = g.gfip_dgemm_ozaki(runner.h.h, "N", "N", 4, 4, 4, 1.0, 16, 4, 16, 4, 0.0, 16, 4, s)
         assert rc == g.GFIP_ERR_ARG
+
+
+def test_wait_timeout_reports_status_and_recovers(runner):
+    """The failure path: with the test hook on, the first CTA withholds one operand copy and
+    its bounded wait runs out after 20 ms.  The call raises GFIP_STATUS_MMA_TIMEOUT, leaves
+    that CTA's 128 x 128 tile of C unwritten, computes every other tile, and the context
+    stays usable: the next call, hook off, is exact again."""
+    p = inputs.problem(95, "N", "N", 300, 260, 200, 1.0, 0.0, 3, 3, 3, dist="int", int_lim=4)
+    ref, _ = gu.reference(p)
+    want = inputs.as_matrix(ref, p.m, p.n, p.ldc)
+    marker = np.where(np.isnan(p.C0), p.C0, 12345.0)     # beta == 0: C is never read
+    A = torch.from_numpy(p.A).to(runner.dev)
+    B = torch.from_numpy(p.B).to(runner.dev)
+    C = torch.from_numpy(marker.copy()).to(runner.dev)
+    runner.h.ensure_ozaki_workspace(p.m, p.n, p.k, 3)
+    assert runner.h.status() == 0
+    assert g.gfip_debug_ozaki_timeout(runner.h.h, True, 20_000_000) == 0
+    try:
+        rc = g.gfip_dgemm_ozaki(runner.h.h, "N", "N", p.m, p.n, p.k, 1.0, A.data_ptr(), p.lda,
+                                B.data_ptr(), p.ldb, 0.0, C.data_ptr(), p.ldc, 3)
+        assert rc == 0
+        torch.cuda.synchronize()
+    finally:
+        assert g.gfip_debug_ozaki_timeout(runner.h.h, False, 0) == 0
+    assert runner.h.status() & g.GFIP_STATUS_MMA_TIMEOUT
+    got = inputs.as_matrix(C.cpu().numpy(), p.m, p.n, p.ldc)
+    assert np.all(got[:128, :128] == 12345.0)            # the withholding CTA's tile
+    rest = np.ones_like(got, dtype=bool)
+    rest[:128, :128] = False
+    assert np.array_equal(got[rest], want[rest])
+    # recovery: same call, hook off
+    C.copy_(torch.from_numpy(marker.copy()))
+    rc = g.gfip_dgemm_ozaki(runner.h.h, "N", "N", p.m, p.n, p.k, 1.0, A.data_ptr(), p.lda,
+                            B.data_ptr(), p.ldb, 0.0, C.data_ptr(), p.ldc, 3)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert runner.h.status() == 0
+    assert np.array_equal(inputs.as_matrix(C.cpu().numpy(), p.m, p.n, p.ldc), want)
