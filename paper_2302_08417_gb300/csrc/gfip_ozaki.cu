@@ -17,11 +17,14 @@
 //            + beta * C_ij,
 // dropping the digit pairs with s + t > S + 1 (triangular truncation).
 //
-// Kernel layout (one CTA per 128 x 128 tile of C, 10 warps):
-//   warp 0      producer: bulk-copies the A- and B-digit tiles (16 KB each, stored already in
-//               the swizzled shared-memory layout the MMA reads) into a 6-stage ring;
-//   warp 1      allocates tensor memory and issues tcgen05.mma (one thread) into one of two
-//               128-column FP32 accumulators, one accumulator per (digit pair, k-chunk);
+// Kernel layout (one CTA per 128 x 128 tile of C, 10 warps).  A "job" is one digit pair
+// (s, t) over one k-chunk, accumulated exactly in one 128-column FP32 accumulator; jobs with
+// the same A digit s run two at a time ("steps"), so a stage holds one A-digit tile and two
+// B-digit tiles and feeds two MMAs:
+//   warp 0      producer: bulk-copies the digit tiles (16 KB each, stored already in the
+//               swizzled shared-memory layout the MMA reads) into a 4-stage ring;
+//   warp 1      allocates tensor memory and issues tcgen05.mma (one thread) into four
+//               128-column FP32 accumulators, two filling while two drain;
 //   warps 2-9   drain a finished accumulator with tcgen05.ld and add it, scaled, into FP64
 //               registers (64 values per thread), then write C.
 // Every mbarrier wait is bounded by a global-timer budget; on a timeout the kernel raises a
@@ -41,22 +44,23 @@ constexpr int TM = 128;              // tile rows (M of the MMA) and digit-tile 
 constexpr int TN = 128;              // tile cols (N of the MMA)
 constexpr int KB = 64;               // k per digit tile: 64 BF16 = one 128-byte row
 constexpr int TILE_BYTES = TM * KB * 2;  // 16 KB per digit tile (A and B alike)
-constexpr int STAGES = 6;
+constexpr int STAGES = 4;
 constexpr int THREADS = 320;
 constexpr int EPI_WARPS = 8;
 constexpr int BETA_BITS = 6;         // bits per digit
 constexpr int KC_BLOCKS = 16384 / KB; // k-blocks per exactly accumulated chunk
-constexpr uint32_t TMEM_COLS = 256;  // two 128-column FP32 accumulators
+constexpr int NACC = 4;              // 128-column FP32 accumulators in tensor memory
+constexpr uint32_t TMEM_COLS = NACC * TN;
 constexpr unsigned STATUS_TIMEOUT = 0x2u;  // mirrors GFIP_STATUS_MMA_TIMEOUT
 constexpr long long WAIT_POLLS = 1ll << 32;  // backstop on polls, should the timer stall
 
 struct Smem {
-    uint8_t a[STAGES][TILE_BYTES];   // 1024-byte aligned (swizzle atoms)
-    uint8_t b[STAGES][TILE_BYTES];
+    uint8_t a[STAGES][TILE_BYTES];      // 1024-byte aligned (swizzle atoms)
+    uint8_t b[STAGES][2][TILE_BYTES];   // the step's one or two B-digit tiles
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
-    uint64_t tfull[2];
-    uint64_t tempty[2];
+    uint64_t tfull[NACC];
+    uint64_t tempty[NACC];
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
@@ -378,24 +382,46 @@ __global__ void __launch_bounds__(256) split_kernel(const double *X, int64_t ld,
 
 // ---- digit-product GEMM with FP64 recombination -----------------------------------------
 
-struct Unit {
-    int s, t, chunk;
+// Work list of one tile, per k-chunk: jobs (s, t), s = 1..S, t = 1..S+1-s, in that order;
+// the jobs of one s form steps of two (the last may be single).
+struct Step {
+    int s, t0, count, job;   // A digit, first B digit, jobs in the step, job index of the first
 };
 
-// Unit u of the work list: digit pairs by level l = s + t (2 .. S+1), then k-chunks.
-__device__ __forceinline__ Unit unit_of(int u, int nchunks)
+__device__ __forceinline__ Step step_of(int q, int slices, int pairs, int steps_per_chunk)
 {
-    Unit x;
-    x.chunk = u % nchunks;
-    int pr = u / nchunks;
-    int l = 2;
-    while (pr >= l - 1) {
-        pr -= l - 1;
-        ++l;
+    const int chunk = q / steps_per_chunk;
+    int r = q - chunk * steps_per_chunk;
+    int before = 0;   // jobs of smaller s in this chunk
+    for (int s = 1; s <= slices; ++s) {
+        const int n = slices + 1 - s, g = (n + 1) / 2;
+        if (r < g) return Step{s, 1 + 2 * r, min(2, n - 2 * r), chunk * pairs + before + 2 * r};
+        r -= g;
+        before += n;
     }
-    x.s = pr + 1;
-    x.t = l - x.s;
-    return x;
+    return Step{0, 0, 0, 0};
+}
+
+struct Job {
+    int s, t;
+};
+
+__device__ __forceinline__ Job job_of(int j, int slices, int pairs)
+{
+    int r = j % pairs;
+    for (int s = 1; s <= slices; ++s) {
+        const int n = slices + 1 - s;
+        if (r < n) return Job{s, 1 + r};
+        r -= n;
+    }
+    return Job{0, 0};
+}
+
+__device__ __forceinline__ int steps_per_chunk(int slices)
+{
+    int g = 0;
+    for (int s = 1; s <= slices; ++s) g += (slices + 2 - s) / 2;
+    return g;
 }
 
 __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
@@ -413,15 +439,17 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
     const int ib = band * GROUP + in_band % rows_in_band;
     const int jb = in_band / rows_in_band;
     const int nchunks = (p.kt + KC_BLOCKS - 1) / KC_BLOCKS;
-    const int npairs = p.slices * (p.slices + 1) / 2;
-    const int units = npairs * nchunks;
+    const int pairs = p.slices * (p.slices + 1) / 2;
+    const int spc = steps_per_chunk(p.slices);
+    const int nsteps = spc * nchunks;
+    const int njobs = pairs * nchunks;
 
     if (tid == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&sm.full[i], 1);
             mbar_init(&sm.empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NACC; ++i) {
             mbar_init(&sm.tfull[i], 1);
             mbar_init(&sm.tempty[i], EPI_WARPS);
         }
@@ -447,9 +475,9 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
             uint32_t phase = 0;
             long long issued = 0;   // stages handed to the copy engine (or withheld)
             const bool withhold = p.inject_timeout && blockIdx.x == 0;
-            for (int u = 0; u < units && !aborted(sm); ++u) {
-                const Unit x = unit_of(u, nchunks);
-                const int k0 = x.chunk * KC_BLOCKS;
+            for (int q = 0; q < nsteps && !aborted(sm); ++q) {
+                const Step x = step_of(q, p.slices, pairs, spc);
+                const int k0 = (q / spc) * KC_BLOCKS;
                 const int k1 = min(p.kt, k0 + KC_BLOCKS);
                 bool ok = true;
                 for (int kb = k0; kb < k1; ++kb) {
@@ -458,13 +486,16 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
                         break;
                     }
                     if (!(withhold && issued == 0)) {
-                        mbar_expect_tx(&sm.full[stage], 2 * TILE_BYTES);
+                        mbar_expect_tx(&sm.full[stage], (1 + x.count) * TILE_BYTES);
                         const uint16_t *ta =
                             p.sa + (((int64_t)(x.s - 1) * p.mt + ib) * p.kt + kb) * (TM * KB);
-                        const uint16_t *tb =
-                            p.sb + (((int64_t)(x.t - 1) * p.nt + jb) * p.kt + kb) * (TN * KB);
                         bulk_copy(sm.a[stage], ta, TILE_BYTES, &sm.full[stage]);
-                        bulk_copy(sm.b[stage], tb, TILE_BYTES, &sm.full[stage]);
+                        for (int c = 0; c < x.count; ++c) {
+                            const uint16_t *tb =
+                                p.sb + (((int64_t)(x.t0 + c - 1) * p.nt + jb) * p.kt + kb) *
+                                           (TN * KB);
+                            bulk_copy(sm.b[stage][c], tb, TILE_BYTES, &sm.full[stage]);
+                        }
                     }
                     ++issued;
                     if (++stage == STAGES) {
@@ -491,27 +522,33 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            for (int u = 0; u < units && !aborted(sm); ++u) {
-                const int buf = u & 1;
-                const uint32_t use = (uint32_t)(u >> 1);
-                if (!mbar_wait(&sm.tempty[buf], (use & 1) ^ 1, sm, p.status, p.wait_ns)) break;
-                tc_fence_after();
-                const Unit x = unit_of(u, nchunks);
-                const int k0 = x.chunk * KC_BLOCKS;
-                const int k1 = min(p.kt, k0 + KC_BLOCKS);
-                const uint32_t dcol = tmem + (uint32_t)(buf * TN);
+            for (int q = 0; q < nsteps && !aborted(sm); ++q) {
+                const Step x = step_of(q, p.slices, pairs, spc);
                 bool ok = true;
+                for (int c = 0; c < x.count && ok; ++c) {
+                    const int j = x.job + c;
+                    ok = mbar_wait(&sm.tempty[j % NACC], ((uint32_t)(j / NACC) & 1u) ^ 1u, sm,
+                                   p.status, p.wait_ns);
+                }
+                if (!ok) break;
+                tc_fence_after();
+                const int k0 = (q / spc) * KC_BLOCKS;
+                const int k1 = min(p.kt, k0 + KC_BLOCKS);
                 for (int kb = k0; kb < k1; ++kb) {
                     if (!mbar_wait(&sm.full[stage], phase, sm, p.status, p.wait_ns)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = saddr(sm.a[stage]), b0 = saddr(sm.b[stage]);
+                    const uint32_t a0 = saddr(sm.a[stage]);
+                    for (int c = 0; c < x.count; ++c) {
+                        const uint32_t dcol = tmem + (uint32_t)(((x.job + c) % NACC) * TN);
+                        const uint32_t b0 = saddr(sm.b[stage][c]);
 #pragma unroll
-                    for (int kk = 0; kk < KB / 16; ++kk)
-                        mma_bf16(dcol, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32),
-                                 (kb > k0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < KB / 16; ++kk)
+                            mma_bf16(dcol, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32),
+                                     (kb > k0 || kk > 0) ? 1u : 0u);
+                    }
                     mma_commit(&sm.empty[stage]);
                     if (++stage == STAGES) {
                         stage = 0;
@@ -519,7 +556,7 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
                     }
                 }
                 if (!ok) break;
-                mma_commit(&sm.tfull[buf]);
+                for (int c = 0; c < x.count; ++c) mma_commit(&sm.tfull[(x.job + c) % NACC]);
             }
             // all MMAs this thread issued have completed once this commit arrives
             mma_commit(&sm.drain);
@@ -532,12 +569,12 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_kernel(const OzakiParams p)
         double acc[64];
 #pragma unroll
         for (int c = 0; c < 64; ++c) acc[c] = 0.0;
-        for (int u = 0; u < units; ++u) {
-            const int buf = u & 1;
-            const uint32_t use = (uint32_t)(u >> 1);
+        for (int j = 0; j < njobs; ++j) {
+            const int buf = j % NACC;
+            const uint32_t use = (uint32_t)(j / NACC);
             if (!mbar_wait(&sm.tfull[buf], use & 1, sm, p.status, p.wait_ns)) break;
             tc_fence_after();
-            const Unit x = unit_of(u, nchunks);
+            const Job x = job_of(j, p.slices, pairs);
             const double scale = ldexp(1.0, -BETA_BITS * (x.s + x.t));
             const uint32_t taddr =
                 tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * TN + half * 64);
