@@ -20,20 +20,21 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gemm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "syrk_oracle.c")]
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile gemm_oracle.c into oracle/_build/liboracle.so (gcc, no contraction)."""
+    """Compile the oracle sources into oracle/_build/liboracle.so (gcc, no contraction)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-std=c99", "-Wall", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+           "-std=c99", "-Wall", "-shared", "-fPIC"] + _SRCS + ["-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -52,6 +53,9 @@ def _load():
                                                 dbl, ptr, i64, ptr, i64, dbl, ptr, i64,
                                                 i64, ptr, ptr, ptr, ctypes.c_int, ctypes.c_int]
             lib.oracle_gemm_entries.restype = ctypes.c_int
+            lib.oracle_syrk.argtypes = [ctypes.c_char, ctypes.c_char, i64, i64, dbl, ptr,
+                                        i64, dbl, ptr, i64]
+            lib.oracle_syrk.restype = ctypes.c_int
             lib.oracle_max_threads.argtypes = []
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -131,3 +135,21 @@ def abs_bound(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc,
     v = entries(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C0, ldc,
                 ii.ravel(), jj.ravel(), absval=True, nthreads=nthreads)
     return v.reshape(m, n)
+
+
+def syrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc) -> int:
+    """In place on C (flat float64, column-major, leading dimension ldc): the triangle uplo of
+    alpha*A*A^T + beta*C (trans 'N', A n x k) or alpha*A^T*A + beta*C (trans 'T', A k x n).
+    Returns 0 or minus the reference-BLAS position of the first bad argument."""
+    lib = _load()
+    return lib.oracle_syrk(uplo.encode(), trans.encode(), n, k, float(alpha),
+                           _ptr(_f64(A, "A")), lda, float(beta), _ptr(_f64(C, "C")), ldc)
+
+
+def syrk_result(uplo, trans, n, k, alpha, A, lda, beta, C0, ldc) -> np.ndarray:
+    """Out-of-place convenience: returns a new flat buffer holding the updated C."""
+    C = np.array(C0, dtype=np.float64, copy=True)
+    rc = syrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc)
+    if rc != 0:
+        raise ValueError(f"oracle_syrk returned {rc}")
+    return C
