@@ -154,6 +154,27 @@ int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, 
                      int64_t k, double alpha, const double *A, int64_t lda, const double *B,
                      int64_t ldb, double beta, double *C, int64_t ldc, int slices);
 
+/* ---- SYRK on the fused kernel (one of the other level-3 operations, Sec. 1 and Sec. 5) ----
+ *
+ * C := alpha * A * A^T + beta * C   (trans 'N', A is n x k, column-major, lda >= max(1, n))
+ * C := alpha * A^T * A + beta * C   (trans 'T' or 'C', A is k x n, lda >= max(1, k))
+ * on the triangle uplo ('L': entries i >= j, 'U': i <= j) of the n x n column-major C
+ * (ldc >= max(1, n)); the other triangle and rows n..ldc-1 are never read or written.  The
+ * same fused kernel as gfip_dgemm computes only the tiles of that triangle, with A in both
+ * operand roles: the first tile line packs each panel of A once and that packed copy serves
+ * as row panel and as column panel.  The pack policy of the handle applies (NONE: raw
+ * reads only).  BLAS rules: beta == 0 does not read C; alpha == 0 or k == 0 does not read A
+ * (C := beta C on the triangle); n == 0 or ((alpha == 0 or k == 0) and beta == 1) returns at
+ * once.  Errors: -1 uplo, -2 trans, -3 n < 0, -4 k < 0, -7 lda, -10 ldc (reference-BLAS
+ * positions), or a GFIP_ERR_* code.  Needs gfip_syrk_workspace_size() bytes of workspace;
+ * asynchronous on the handle's stream. */
+size_t gfip_syrk_workspace_size(gfip_handle_t handle, char uplo, char trans, int64_t n,
+                                int64_t k, int elem_bytes);
+int gfip_dsyrk(gfip_handle_t handle, char uplo, char trans, int64_t n, int64_t k, double alpha,
+               const double *A, int64_t lda, double beta, double *C, int64_t ldc);
+int gfip_ssyrk(gfip_handle_t handle, char uplo, char trans, int64_t n, int64_t k, float alpha,
+               const float *A, int64_t lda, float beta, float *C, int64_t ldc);
+
 /* Test hook for the failure path of gfip_dgemm_ozaki (no counterpart in the paper; the
  * paper's CPU kernels have no waits).  Sets, for this handle's later gfip_dgemm_ozaki calls,
  * the budget of every pipeline wait in nanoseconds (0 restores the default, 2 s), and with

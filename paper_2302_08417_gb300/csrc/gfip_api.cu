@@ -88,6 +88,7 @@ enum class Variant { Fused, Direct, PackThenCompute };
 
 template <typename T> struct Plan {
     int mt = 0, nt = 0, kt = 0, tiles = 0;
+    int tri = gfip::TRI_NONE;   // triangle of C computed (SYRK), else the whole rectangle
     int grid = 0, dp_tiles = 0;
     int64_t sk_iters = 0;
     int mode_a = gfip::MODE_RAW, mode_b = gfip::MODE_RAW;
@@ -105,14 +106,16 @@ template <typename T> int blocks_per_sm(Handle *h)
 }
 
 template <typename T>
-Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
+Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI_NONE)
 {
     using Cfg = gfip::TileCfg<T>;
     Plan<T> pl;
     pl.mt = (m + Cfg::BM - 1) / Cfg::BM;
     pl.nt = (n + Cfg::BN - 1) / Cfg::BN;
     pl.kt = (k + Cfg::BK - 1) / Cfg::BK;
-    pl.tiles = pl.mt * pl.nt;
+    pl.tri = tri;
+    // a triangle (m == n, square tiles) holds the tiles on and on one side of the diagonal
+    pl.tiles = tri ? pl.mt * (pl.mt + 1) / 2 : pl.mt * pl.nt;
 
     // Schedule: data-parallel waves of whole tiles, then the remaining tiles (the partial
     // wave plus one full wave) split evenly along k over all CTAs.
@@ -177,6 +180,12 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
         }
         break;
     }
+    if (tri) {
+        // SYRK: both operand roles read panels of the same matrix A, so one packed copy
+        // serves both; any packing policy packs A's panels once (or not at all)
+        const bool pack = (pl.mode_a != gfip::MODE_RAW) || (pl.mode_b != gfip::MODE_RAW);
+        pl.mode_a = pl.mode_b = pack ? gfip::MODE_FIP : gfip::MODE_RAW;
+    }
 
     // Control region: header, arrival counters of split tiles, ready words of packed tiles.
     size_t off = kHeader;
@@ -184,8 +193,9 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
     off += round_up((size_t)pl.tiles * 8, kAlign);
     pl.off_state_a = off;
     if (pl.mode_a == gfip::MODE_FIP) off += round_up((size_t)pl.mt * (pl.kt + 1) * 8, kAlign);
-    pl.off_state_b = off;
-    if (pl.mode_b == gfip::MODE_FIP) off += round_up((size_t)pl.nt * (pl.kt + 1) * 8, kAlign);
+    pl.off_state_b = tri ? pl.off_state_a : off;
+    if (pl.mode_b == gfip::MODE_FIP && !tri)
+        off += round_up((size_t)pl.nt * (pl.kt + 1) * 8, kAlign);
     pl.ctrl_needed = off;
 
     // Data region (relative to its start): partial sums, packed A, packed B.
@@ -195,8 +205,8 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k)
     pl.data_pack_a = d;
     if (pl.mode_a != gfip::MODE_RAW)
         d += round_up((size_t)pl.mt * pl.kt * Cfg::BM * Cfg::BK * sizeof(T), kAlign);
-    pl.data_pack_b = d;
-    if (pl.mode_b != gfip::MODE_RAW)
+    pl.data_pack_b = tri ? pl.data_pack_a : d;
+    if (pl.mode_b != gfip::MODE_RAW && !tri)
         d += round_up((size_t)pl.nt * pl.kt * Cfg::BN * Cfg::BK * sizeof(T), kAlign);
     pl.data_bytes = d;
     return pl;
@@ -212,6 +222,11 @@ bool too_big(int64_t v)
 {
     return v > std::numeric_limits<int32_t>::max();
 }
+
+template <typename T>
+int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t m, int64_t n,
+                int64_t k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb, T beta,
+                T *C, int64_t ldc);
 
 template <typename T>
 int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_t m, int64_t n,
@@ -231,14 +246,24 @@ int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_
         return GFIP_ERR_SIZE;
     if (C == nullptr) return GFIP_ERR_NULLPTR;
     if (!use_ab) {
-        if (gfip::launch_scale<T>(C, ldc, (int)m, (int)n, beta, h->stream) != cudaSuccess)
+        if (gfip::launch_scale<T>(C, ldc, (int)m, (int)n, beta, gfip::TRI_NONE, h->stream) != cudaSuccess)
             return GFIP_ERR_CUDA;
         h->last_launches = 1;
         return GFIP_OK;
     }
     if (A == nullptr || B == nullptr) return GFIP_ERR_NULLPTR;
+    return launch_plan<T>(h, v, gfip::TRI_NONE, transa, transb, m, n, k, alpha, A, lda, B, ldb,
+                          beta, C, ldc);
+}
 
-    Plan<T> pl = make_plan<T>(h, v, (int)m, (int)n, (int)k);
+// Plans and launches one GEMM (or the triangle `tri` of one) whose arguments are checked
+// and whose quick returns are taken.
+template <typename T>
+int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t m, int64_t n,
+                int64_t k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb, T beta,
+                T *C, int64_t ldc)
+{
+    Plan<T> pl = make_plan<T>(h, v, (int)m, (int)n, (int)k, tri);
     if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
     if (total_bytes(h, pl) > h->ws_bytes) return GFIP_ERR_WORKSPACE;
 
@@ -279,6 +304,11 @@ int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_
     p.sk_iters = pl.sk_iters;
     p.mode_a = pl.mode_a;
     p.mode_b = pl.mode_b;
+    p.tri = tri;
+    // the operand whose first tile line packs: A (first tile column) unless the triangle is
+    // the upper one, whose first tile line is the first tile row (B's producers)
+    p.a_produces = (tri != gfip::TRI_UPPER) ? 1 : 0;
+    p.b_produces = (tri == gfip::TRI_NONE || tri == gfip::TRI_UPPER) ? 1 : 0;
     p.state_a = reinterpret_cast<unsigned long long *>(h->ws + pl.off_state_a);
     p.state_b = reinterpret_cast<unsigned long long *>(h->ws + pl.off_state_b);
     p.tile_count = reinterpret_cast<unsigned long long *>(h->ws + pl.off_count);
@@ -357,6 +387,70 @@ size_t workspace_size_impl(Handle *h, char transa, char transb, int64_t m, int64
     if (too_big(m) || too_big(n) || too_big(k)) return 0;
     if (m == 0 || n == 0 || k == 0) return round_up(kHeader, kCtrlGranule);
     const Plan<T> pl = make_plan<T>(h, v, (int)m, (int)n, (int)k);
+    return total_bytes(h, pl);
+}
+
+// Reference-BLAS dsyrk argument check: 0, or minus the 1-based position of the first bad
+// argument in (uplo, trans, n, k, alpha, A, lda, beta, C, ldc).
+int check_syrk(char uplo, char trans, int64_t n, int64_t k, int64_t lda, int64_t ldc)
+{
+    const bool up_ok = uplo == 'L' || uplo == 'l' || uplo == 'U' || uplo == 'u';
+    const bool tr_ok = trans == 'N' || trans == 'n' || trans == 'T' || trans == 't' ||
+                       trans == 'C' || trans == 'c';
+    if (!up_ok) return -1;
+    if (!tr_ok) return -2;
+    if (n < 0) return -3;
+    if (k < 0) return -4;
+    const int64_t rows_a = is_notrans(trans) ? n : k;
+    if (lda < std::max<int64_t>(1, rows_a)) return -7;
+    if (ldc < std::max<int64_t>(1, n)) return -10;
+    return 0;
+}
+
+// SYRK on the fused kernel: op(A) op(A)^T with the same matrix in both operand roles, only
+// the tiles of the requested triangle, and one packed copy per panel of A serving both roles.
+template <typename T>
+int syrk_entry(gfip_handle_t handle, char uplo, char trans, int64_t n, int64_t k, T alpha,
+               const T *A, int64_t lda, T beta, T *C, int64_t ldc)
+{
+    const int info = check_syrk(uplo, trans, n, k, lda, ldc);
+    if (info != 0) return info;
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    h->last_launches = 0;
+    h->last_grid = 0;
+    if (n == 0) return GFIP_OK;
+    const bool use_ab = !(alpha == T(0) || k == 0);
+    if (!use_ab && beta == T(1)) return GFIP_OK;
+    if (too_big(n) || too_big(k) || too_big(lda) || too_big(ldc)) return GFIP_ERR_SIZE;
+    if (C == nullptr) return GFIP_ERR_NULLPTR;
+    const int tri = (uplo == 'L' || uplo == 'l') ? gfip::TRI_LOWER : gfip::TRI_UPPER;
+    if (!use_ab) {
+        if (gfip::launch_scale<T>(C, ldc, (int)n, (int)n, beta, tri, h->stream) != cudaSuccess)
+            return GFIP_ERR_CUDA;
+        h->last_launches = 1;
+        return GFIP_OK;
+    }
+    if (A == nullptr) return GFIP_ERR_NULLPTR;
+    // trans 'N': C = A A^T  -> op(A) = A ('N'), op(B) = A^T ('T' on the same storage);
+    // trans 'T': C = A^T A  -> op(A) = A^T ('T'), op(B) = A ('N')
+    const char ta = is_notrans(trans) ? 'N' : 'T';
+    const char tb = is_notrans(trans) ? 'T' : 'N';
+    return launch_plan<T>(h, Variant::Fused, tri, ta, tb, n, n, k, alpha, A, lda, A, lda, beta,
+                          C, ldc);
+}
+
+template <typename T>
+size_t syrk_workspace_impl(Handle *h, char uplo, char trans, int64_t n, int64_t k)
+{
+    const int64_t rows_a = is_notrans(trans) ? n : k;
+    if (check_syrk(uplo, trans, n, k, std::max<int64_t>(1, rows_a), std::max<int64_t>(1, n)) !=
+        0)
+        return 0;
+    if (too_big(n) || too_big(k)) return 0;
+    if (n == 0 || k == 0) return round_up(kHeader, kCtrlGranule);
+    const int tri = (uplo == 'L' || uplo == 'l') ? gfip::TRI_LOWER : gfip::TRI_UPPER;
+    const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)n, (int)n, (int)k, tri);
     return total_bytes(h, pl);
 }
 
@@ -456,6 +550,28 @@ int gfip_set_pack_policy(gfip_handle_t handle, int policy)
     return GFIP_OK;
 }
 
+size_t gfip_syrk_workspace_size(gfip_handle_t handle, char uplo, char trans, int64_t n,
+                                int64_t k, int elem_bytes)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return 0;
+    if (elem_bytes == 8) return syrk_workspace_impl<double>(h, uplo, trans, n, k);
+    if (elem_bytes == 4) return syrk_workspace_impl<float>(h, uplo, trans, n, k);
+    return 0;
+}
+
+int gfip_dsyrk(gfip_handle_t handle, char uplo, char trans, int64_t n, int64_t k, double alpha,
+               const double *A, int64_t lda, double beta, double *C, int64_t ldc)
+{
+    return syrk_entry<double>(handle, uplo, trans, n, k, alpha, A, lda, beta, C, ldc);
+}
+
+int gfip_ssyrk(gfip_handle_t handle, char uplo, char trans, int64_t n, int64_t k, float alpha,
+               const float *A, int64_t lda, float beta, float *C, int64_t ldc)
+{
+    return syrk_entry<float>(handle, uplo, trans, n, k, alpha, A, lda, beta, C, ldc);
+}
+
 int gfip_dgemm(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n, int64_t k,
                double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
                double beta, double *C, int64_t ldc)
@@ -536,13 +652,14 @@ const char *gfip_error_string(int code)
 {
     if (code < 0) {
         switch (code) {
-        case -1: return "invalid argument 1 (transa)";
-        case -2: return "invalid argument 2 (transb)";
-        case -3: return "invalid argument 3 (m < 0)";
-        case -4: return "invalid argument 4 (n < 0)";
+        case -1: return "invalid argument 1 (transa of gemm, uplo of syrk)";
+        case -2: return "invalid argument 2 (transb of gemm, trans of syrk)";
+        case -3: return "invalid argument 3 (m < 0 of gemm, n < 0 of syrk)";
+        case -4: return "invalid argument 4 (n < 0 of gemm, k < 0 of syrk)";
         case -5: return "invalid argument 5 (k < 0)";
         case -8: return "invalid argument 8 (lda < max(1, rows of A))";
-        case -10: return "invalid argument 10 (ldb < max(1, rows of B))";
+        case -7: return "invalid argument 7 (lda of syrk < max(1, rows of A))";
+        case -10: return "invalid argument 10 (ldb of gemm < max(1, rows of B), ldc of syrk < max(1, n))";
         case -13: return "invalid argument 13 (ldc < max(1, m))";
         default: return "invalid argument";
         }
@@ -597,7 +714,7 @@ int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, 
     if (too_big(m) || too_big(n) || too_big(k)) return GFIP_ERR_SIZE;
     if (C == nullptr) return GFIP_ERR_NULLPTR;
     if (!use_ab) {
-        if (gfip::launch_scale<double>(C, ldc, (int)m, (int)n, beta, h->stream) != cudaSuccess)
+        if (gfip::launch_scale<double>(C, ldc, (int)m, (int)n, beta, gfip::TRI_NONE, h->stream) != cudaSuccess)
             return GFIP_ERR_CUDA;
         h->last_launches = 1;
         return GFIP_OK;

@@ -8,11 +8,15 @@
 namespace gfip {
 
 // Where an operand's tiles come from in one launch of the GEMM kernel.
+// Part of C a launch computes: all of it (GEMM), or one triangle of a square C (SYRK).
+enum Triangle : int { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
+
 enum OperandMode : int {
     MODE_RAW = 0,     // always read the raw strided operand (direct variant, SUP analog)
     MODE_PACKED = 1,  // always read the packed copy, written beforehand by the pack kernel
-    MODE_FIP = 2,     // fused: the first CTA to touch a (panel, k-block) packs it, later
-                      // touches read the packed copy (Sec. 3.1 Alg. 1, Sec. 3.2, Sec. 3.5)
+    MODE_FIP = 2,     // fused: the first tile line packs each (panel, k-block) while
+                      // computing with it, later tiles read the packed copy once it is
+                      // published (Sec. 3.1 Alg. 1, Sec. 3.2)
 };
 
 // Tile shape of one element type.  The CTA computes a BM x BN tile of C, stepping through
@@ -86,6 +90,9 @@ template <typename T> struct GemmParams {
     int mt, nt, kt;   // tile counts along m, n and k
     int tiles;        // mt * nt
     int band;         // tile rows per band of the consumer tile order (>= 1)
+    int tri;          // TRI_NONE: all of C; TRI_LOWER / TRI_UPPER: that triangle (SYRK)
+    int a_produces;   // the first tile column packs the A panels
+    int b_produces;   // the first tile row packs the B panels
     int grid;         // persistent CTAs
     int dp_tiles;     // tiles [0, dp_tiles) are data-parallel: tile t runs on CTA t % grid
     int64_t sk_iters; // (tiles - dp_tiles) * kt iterations split evenly over the CTAs
@@ -149,7 +156,7 @@ cudaError_t launch_grouped(const GroupParams<T> &gp, int tile, cudaStream_t s);
 template <typename T> cudaError_t launch_gemm(const GemmParams<T> &p, cudaStream_t s);
 template <typename T> cudaError_t launch_pack(const PackParams<T> &p, cudaStream_t s);
 template <typename T>
-cudaError_t launch_scale(T *C, int64_t ldc, int m, int n, T beta, cudaStream_t s);
+cudaError_t launch_scale(T *C, int64_t ldc, int m, int n, T beta, int tri, cudaStream_t s);
 // CTAs of the GEMM kernel that fit on one SM at once.
 template <typename T> int gemm_blocks_per_sm();
 

@@ -274,6 +274,43 @@ __device__ __forceinline__ void tile_coords(int t, int mt, int nt, int band, int
     j = 1 + r / h;
 }
 
+
+// Tile order of a triangle of a square tile grid (mt x mt), producers first: the first tile
+// column (t < mt: (t, 0)), then the other tiles (i, j), 1 <= j <= i, column by column.  The
+// upper triangle is the transpose: (j, i), whose first tile row holds the producers.
+__device__ __forceinline__ void tri_coords(int t, int mt, int tri, int &i, int &j)
+{
+    int a, b;
+    if (t < mt) {
+        a = t;
+        b = 0;
+    } else {
+        t -= mt;
+        b = 1;
+        while (t >= mt - b) {   // column b holds rows b .. mt-1
+            t -= mt - b;
+            ++b;
+        }
+        a = b + t;
+    }
+    if (tri == TRI_UPPER) {
+        i = b;
+        j = a;
+    } else {
+        i = a;
+        j = b;
+    }
+}
+
+// The (i, j) of tile t in the launch's order.
+template <typename P> __device__ __forceinline__ void tile_of(const P &p, int t, int &i, int &j)
+{
+    if (p.tri != TRI_NONE)
+        tri_coords(t, p.mt, p.tri, i, j);
+    else
+        tile_coords(t, p.mt, p.nt, p.band, i, j);
+}
+
 template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     using Cfg = C;
     T a[Cfg::STAGES][TileLayout<T, Cfg::BM, Cfg::BK>::ELEMS];
@@ -340,6 +377,23 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         return word == ready_value(epoch) ? DEC_PACKED : DEC_RAW;
     }
 
+    // Is C[row, col] inside the part of C the launch computes (the whole of C, or a triangle)?
+    static __device__ __forceinline__ bool in_tri(const GemmParams<T> &p, int row, int col)
+    {
+        return p.tri == TRI_NONE || (p.tri == TRI_LOWER ? row >= col : row <= col);
+    }
+
+    // Producers: the first tile column packs the A panels, the first tile row the B panels
+    // (Alg. 1), unless the launch reads that operand from the other one's packed copy.
+    static __device__ __forceinline__ bool prod_a(const GemmParams<T> &p, int j)
+    {
+        return j == 0 && p.a_produces;
+    }
+    static __device__ __forceinline__ bool prod_b(const GemmParams<T> &p, int i)
+    {
+        return i == 0 && p.b_produces;
+    }
+
     struct Words {
         unsigned long long a, b;
     };
@@ -349,9 +403,9 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                                                         int kb)
     {
         Words w{0ull, 0ull};
-        if (need_word(p.mode_a, j == 0, sm.full_a))
+        if (need_word(p.mode_a, prod_a(p, j), sm.full_a))
             w.a = ld_relaxed(p.state_a + (int64_t)i * p.kt + kb);
-        if (need_word(p.mode_b, i == 0, sm.full_b))
+        if (need_word(p.mode_b, prod_b(p, i), sm.full_b))
             w.b = ld_relaxed(p.state_b + (int64_t)j * p.kt + kb);
         return w;
     }
@@ -362,8 +416,8 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                                                            Smem &sm, int i, int j,
                                                            Words w, int q, unsigned int epoch)
     {
-        const int da = classify(p.mode_a, j == 0, sm.full_a, w.a, epoch);
-        const int db = classify(p.mode_b, i == 0, sm.full_b, w.b, epoch);
+        const int da = classify(p.mode_a, prod_a(p, j), sm.full_a, w.a, epoch);
+        const int db = classify(p.mode_b, prod_b(p, i), sm.full_b, w.b, epoch);
         sm.dec_a[q % DEC] = da;
         sm.dec_b[q % DEC] = db;
         return (da == DEC_PACKED && p.mode_a == MODE_FIP && !sm.full_a) ||
@@ -507,9 +561,9 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
 
         if (tid == 0) {
             // a panel whose producer finished it whole needs no per-k-block look-ups
-            const bool fa = need_word(p.mode_a, j == 0, 0) &&
+            const bool fa = need_word(p.mode_a, prod_a(p, j), 0) &&
                             ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) == ready_value(epoch);
-            const bool fb = need_word(p.mode_b, i == 0, 0) &&
+            const bool fb = need_word(p.mode_b, prod_b(p, i), 0) &&
                             ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) == ready_value(epoch);
             sm.full_a = fa;
             sm.full_b = fb;
@@ -561,9 +615,9 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             publish_produced(p, sm, i, j, kb0, nkb - 1, epoch);
             // a producer that covered its whole panel publishes the panel as complete
             if (kb0 == 0 && kb1 == p.kt) {
-                if (p.mode_a == MODE_FIP && j == 0)
+                if (p.mode_a == MODE_FIP && prod_a(p, j))
                     publish(p.state_a + (int64_t)p.mt * p.kt + i, epoch);
-                if (p.mode_b == MODE_FIP && i == 0)
+                if (p.mode_b == MODE_FIP && prod_b(p, i))
                     publish(p.state_b + (int64_t)p.nt * p.kt + j, epoch);
             }
         }
@@ -589,12 +643,12 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
 #pragma unroll
             for (int ii = 0; ii < TM; ++ii) {
                 const int row = m0 + tx * CH + (ii % CH) + (ii / CH) * (BM / NCM);
-                c[ii] = (read_c && row < p.m) ? ccol[row] : T(0);
+                c[ii] = (read_c && row < p.m && in_tri(p, row, col)) ? ccol[row] : T(0);
             }
 #pragma unroll
             for (int ii = 0; ii < TM; ++ii) {
                 const int row = m0 + tx * CH + (ii % CH) + (ii / CH) * (BM / NCM);
-                if (row >= p.m) continue;
+                if (row >= p.m || !in_tri(p, row, col)) continue;
                 T v = p.alpha * acc[ii][jj];
                 if (read_c) v = fma(p.beta, c[ii], v);
                 ccol[row] = v;
@@ -684,7 +738,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         T acc[TM][TN];
         for (int t = g; t < p.dp_tiles; t += p.grid) {
             int i, j;
-            tile_coords(t, p.mt, p.nt, p.band, i, j);
+            tile_of(p, t, i, j);
             run_segment(p, sm, i, j, 0, p.kt, acc, epoch);
             epilogue(p, i, j, acc);
             __syncthreads();
@@ -697,7 +751,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                 const int u = static_cast<int>(q / p.kt);
                 const int t = p.dp_tiles + u;
                 int i, j;
-                tile_coords(t, p.mt, p.nt, p.band, i, j);
+                tile_of(p, t, i, j);
                 const int kb0 = static_cast<int>(q % p.kt);
                 const int64_t rest = hi - q;
                 const int kb1 =
@@ -780,14 +834,16 @@ __global__ void __launch_bounds__(TileCfg<T>::THREADS) pack_kernel(const PackPar
     }
 }
 
-// C := beta*C on the m x n region (beta == 0 writes zeros without reading C).
+// C := beta*C on the m x n region, or on one triangle of it (beta == 0 writes zeros without
+// reading C).
 template <typename T>
-__global__ void scale_kernel(T *C, int64_t ldc, int m, int n, T beta)
+__global__ void scale_kernel(T *C, int64_t ldc, int m, int n, T beta, int tri)
 {
     const int64_t total = (int64_t)m * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t col = e / m, row = e % m;
+        if ((tri == TRI_LOWER && row < col) || (tri == TRI_UPPER && row > col)) continue;
         T *c = C + row + col * ldc;
         *c = (beta == T(0)) ? T(0) : beta * *c;
     }
@@ -870,14 +926,15 @@ template <typename T> cudaError_t launch_pack_impl(const PackParams<T> &p, cudaS
 }
 
 template <typename T>
-cudaError_t launch_scale_impl(T *C, int64_t ldc, int m, int n, T beta, cudaStream_t s)
+cudaError_t launch_scale_impl(T *C, int64_t ldc, int m, int n, T beta, int tri, cudaStream_t s)
 {
     const int64_t total = (int64_t)m * n;
     const int threads = 256;
     int64_t blocks = (total + threads - 1) / threads;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    scale_kernel<T><<<static_cast<unsigned int>(blocks), threads, 0, s>>>(C, ldc, m, n, beta);
+    scale_kernel<T><<<static_cast<unsigned int>(blocks), threads, 0, s>>>(C, ldc, m, n, beta,
+                                                                        tri);
     return cudaGetLastError();
 }
 
@@ -895,9 +952,10 @@ cudaError_t launch_scale_impl(T *C, int64_t ldc, int m, int n, T beta, cudaStrea
         return launch_pack_impl<T>(p, s);                                                     \
     }                                                                                         \
     template <>                                                                               \
-    cudaError_t launch_scale<T>(T * C, int64_t ldc, int m, int n, T beta, cudaStream_t s)     \
+    cudaError_t launch_scale<T>(T * C, int64_t ldc, int m, int n, T beta, int tri,            \
+                                cudaStream_t s)                                               \
     {                                                                                         \
-        return launch_scale_impl<T>(C, ldc, m, n, beta, s);                                   \
+        return launch_scale_impl<T>(C, ldc, m, n, beta, tri, s);                              \
     }                                                                                         \
     template <> int gemm_blocks_per_sm<T>()                                                   \
     {                                                                                         \

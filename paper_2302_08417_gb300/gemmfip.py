@@ -64,6 +64,9 @@ SIGNATURES = {
     "gfip_sgemm_grouped": (_int, [_ptr, _int] + [_ptr] * 13 + [_int]),
     "gfip_dgemm_ozaki": (_int, _GEMM_D + [_int]),
     "gfip_debug_ozaki_timeout": (_int, [_ptr, _int, ctypes.c_uint64]),
+    "gfip_syrk_workspace_size": (_sz, [_ptr, _chr, _chr, _i64, _i64, _int]),
+    "gfip_dsyrk": (_int, [_ptr, _chr, _chr, _i64, _i64, _dbl, _ptr, _i64, _dbl, _ptr, _i64]),
+    "gfip_ssyrk": (_int, [_ptr, _chr, _chr, _i64, _i64, _flt, _ptr, _i64, _flt, _ptr, _i64]),
 }
 
 _lock = threading.Lock()
@@ -201,6 +204,16 @@ def gfip_debug_ozaki_timeout(handle, enable: bool, wait_ns: int = 0) -> int:
     return load().gfip_debug_ozaki_timeout(handle, int(bool(enable)), int(wait_ns))
 
 
+def gfip_syrk_workspace_size(handle, uplo, trans, n, k, elem_bytes) -> int:
+    return load().gfip_syrk_workspace_size(handle, _b(uplo), _b(trans), n, k, elem_bytes)
+
+
+def gfip_syrk(esz, handle, uplo, trans, n, k, alpha, A, lda, beta, C, ldc) -> int:
+    """gfip_dsyrk (esz 8) or gfip_ssyrk (esz 4); A and C are device pointers."""
+    fn = load().gfip_dsyrk if esz == 8 else load().gfip_ssyrk
+    return fn(handle, _b(uplo), _b(trans), n, k, alpha, A or None, lda, beta, C or None, ldc)
+
+
 def gfip_grouped_workspace_size(handle, count) -> int:
     return load().gfip_grouped_workspace_size(handle, count)
 
@@ -244,6 +257,13 @@ class Handle:
 
     def ensure_workspace(self, transa, transb, m, n, k, elem_bytes):
         need = gfip_workspace_size(self.h, transa, transb, m, n, k, elem_bytes)
+        if self.workspace is None or self.workspace.numel() < need:
+            if self.workspace is not None:
+                self._torch.cuda.current_stream().synchronize()
+            self._set_ws(int(need * 1.25) + (1 << 20))
+
+    def ensure_syrk_workspace(self, uplo, trans, n, k, elem_bytes):
+        need = gfip_syrk_workspace_size(self.h, uplo, trans, n, k, elem_bytes)
         if self.workspace is None or self.workspace.numel() < need:
             if self.workspace is not None:
                 self._torch.cuda.current_stream().synchronize()
@@ -380,4 +400,34 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, transa: str = "N",
                     beta, C.data_ptr(), ldc)
     if rc != GFIP_OK:
         raise GemmError(rc, name)
+    return C
+
+
+def syrk(A, C=None, alpha: float = 1.0, beta: float = 0.0, uplo: str = "L", trans: str = "N",
+         handle: Handle | None = None):
+    """The triangle ``uplo`` of ``C := alpha*A*A^T + beta*C`` (trans 'N', A n x k) or
+    ``alpha*A^T*A + beta*C`` (trans 'T', A k x n) on column-major CUDA tensors; the other
+    triangle of C is left as it is (allocated, and left uninitialised, when C is None; beta
+    must then be 0).  Asynchronous on torch's current stream.  Returns C."""
+    import torch
+    dtype = A.dtype
+    if dtype not in (torch.float64, torch.float32):
+        raise TypeError("A must be float64 or float32")
+    esz = 8 if dtype == torch.float64 else 4
+    tr, up = trans.upper(), uplo.upper()
+    n = A.shape[0] if tr == "N" else A.shape[1]
+    k = A.shape[1] if tr == "N" else A.shape[0]
+    if C is None:
+        if beta != 0.0:
+            raise ValueError("C is required when beta != 0")
+        C = torch.empty((n, n), dtype=dtype, device=A.device).t()
+    if C.dtype != dtype or tuple(C.shape) != (n, n):
+        raise ValueError(f"C must be {n}x{n} {dtype}")
+    lda, ldc = _colmajor_ld(A, "A"), _colmajor_ld(C, "C")
+    h = handle or default_handle()
+    h.bind_stream()
+    h.ensure_syrk_workspace(up, tr, n, k, esz)
+    rc = gfip_syrk(esz, h.h, up, tr, n, k, alpha, A.data_ptr(), lda, beta, C.data_ptr(), ldc)
+    if rc != GFIP_OK:
+        raise GemmError(rc, "gfip_syrk")
     return C
