@@ -604,6 +604,67 @@ def autograd_report(torch, shapes=((4096, 4096, 1024), (1024, 8192, 4096)), coun
     return out
 
 
+def syrk_report(g, torch, shapes=((8192, 8192), (2048, 2048))):
+    """SYRK (lower, trans 'N', beta 0.5, ld = n + 7) on the fused kernel: GFLOP/s counted as
+    n(n+1)k (the triangle), with A's panels packed once for both operand roles (policy AUTO)
+    and with raw reads only (policy NONE), against the full GEMM of the same shape.  Device
+    time, CUDA events, best of a few calls."""
+    out = {"note": "uplo L, trans N, beta 0.5, ld = n + 7; flops n(n+1)k; GEMM = the full "
+                   "n x n x k product with the same operands"}
+    h = g.Handle()
+    h.bind_stream()
+    for dtype, tag in ((torch.float64, "f64"), (torch.float32, "f32")):
+        esz = 8 if tag == "f64" else 4
+        rows = {}
+        for n, k in shapes:
+            A, _, C = make_operands(n + k, dtype, n, n, k)
+            lda, ldc = A.stride(1), C.stride(1)
+            h.ensure_syrk_workspace("L", "N", n, k, esz)
+            h.ensure_workspace("N", "T", n, n, k, esz)
+
+            def best(fn, reps):
+                fn()
+                torch.cuda.synchronize()
+                t = float("inf")
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    fn()
+                    e1.record()
+                    e1.synchronize()
+                    t = min(t, e0.elapsed_time(e1))
+                return t
+            r = {}
+            for pol, name in ((g.GFIP_PACK_AUTO, "fused"), (g.GFIP_PACK_NONE, "raw_only")):
+                h.set_pack_policy(pol)
+
+                def call():
+                    rc = g.gfip_syrk(esz, h.h, "L", "N", n, k, 1.0, A.data_ptr(), lda, 0.5,
+                                     C.data_ptr(), ldc)
+                    assert rc == 0, rc
+                ms = best(call, 2 if n * n * k > 2 ** 36 else 5)
+                r[name] = round(n * (n + 1) * k / 1e9 / (ms * 1e-3), 1)
+                r[name + "_ms"] = round(ms, 3)
+            h.set_pack_policy(g.GFIP_PACK_AUTO)
+            gname = g.ENTRY[("fused", esz)]
+
+            def gcall():
+                rc = g._gemm_call(gname, h.h, "N", "T", n, n, k, 1.0, A.data_ptr(), lda,
+                                  A.data_ptr(), lda, 0.5, C.data_ptr(), ldc)
+                assert rc == 0, rc
+            gms = best(gcall, 2 if n * n * k > 2 ** 36 else 5)
+            r["gemm_ms"] = round(gms, 3)
+            r["syrk_time_over_gemm"] = round(r["fused_ms"] / gms, 3)
+            peak = FP64_PEAK_GFLOPS if tag == "f64" else FP32_PEAK_GFLOPS
+            r["fused_frac_of_peak"] = round(r["fused"] / peak, 4)
+            rows[f"{n}x{k}"] = r
+            del A, C
+        out[tag] = rows
+    out["status"] = h.status()
+    return out
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -675,6 +736,8 @@ def main():
                     help="only run the grouped-GEMM report on COUNT problems")
     ap.add_argument("--autograd-only", action="store_true",
                     help="only run the differentiable-GEMM report")
+    ap.add_argument("--syrk-only", action="store_true", help="only run the SYRK report")
+    ap.add_argument("--no-syrk", action="store_true")
     ap.add_argument("--no-autograd", action="store_true")
     args = ap.parse_args()
     if args.size != M or args.dtype != "f64" or args.variant != "fused":
@@ -699,8 +762,10 @@ def main():
     h = g.Handle()
     h.bind_stream()
     stream = torch.cuda.current_stream()
-    if args.emulation_only or args.batched_only or args.autograd_only:
+    if args.emulation_only or args.batched_only or args.autograd_only or args.syrk_only:
         out = {}
+        if args.syrk_only:
+            out["syrk"] = syrk_report(g, torch)
         if args.autograd_only:
             out["autograd"] = autograd_report(torch)
         if args.emulation_only:
@@ -829,6 +894,8 @@ def main():
         result["batched"] = batched_report(g, torch)
     if rank == 0 and not args.no_autograd:
         result["autograd"] = autograd_report(torch)
+    if rank == 0 and not args.no_syrk:
+        result["syrk"] = syrk_report(g, torch)
     if rank == 0 and not args.no_spectrum:
         result["spectrum_gflops"] = spectrum(h, g, torch)
         result["spectrum_gflops"]["note"] = ("N/N, ld = m + 7, beta = 0.5, best of a few "
