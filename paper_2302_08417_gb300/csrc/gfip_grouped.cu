@@ -14,6 +14,7 @@
 //            binary search in the prefix sums and runs the data-parallel tile core
 //            (raw strided operands, whole k loop, alpha/beta epilogue)
 #include <cstdint>
+#include <type_traits>
 
 #include "gfip_grouped.h"
 #include "gfip_kernels.cuh"
@@ -118,7 +119,10 @@ __device__ __forceinline__ void grouped_tile(const GroupDesc<T> &d, GemmSmem<T, 
     p.mode_a = MODE_RAW;
     p.mode_b = MODE_RAW;
     typename K::AccT acc;
-    K::run_segment(p, sm, i, j, 0, d.kt, acc, 0u);
+    // the half-height micro-tile pays where the pipe is the bound and registers allow it:
+    // FP64 (DFMA-bound) and the 64-thread FP32 tile, not the 128-register FP32 tile
+    constexpr bool HALF_ROWS = std::is_same<T, double>::value || Cfg::THREADS <= 64;
+    K::template run_segment<HALF_ROWS>(p, sm, i, j, 0, d.kt, acc, 0u);
     K::epilogue(p, i, j, acc);
 }
 

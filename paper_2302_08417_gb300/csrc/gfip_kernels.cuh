@@ -450,8 +450,12 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
     // acc += As^T Bs over the BK rows of one stage.  Fragment addresses are a per-thread base
     // plus kk * P; the loop is unrolled UNROLL rows at a time to bound the code size.
     static constexpr int UNROLL = BK < Cfg::UNROLL ? BK : Cfg::UNROLL;
+    // Only the first NMA of the NCM row chunks and the first kext rows of k (a multiple of
+    // UNROLL) are computed: a fringe tile skips rows past m and k-rows past k, which hold
+    // zero padding or belong to rows that are never stored.
+    template <int NMA>
     static __device__ __forceinline__ void compute(const T *As, const T *Bs, T (&acc)[TM][TN],
-                                                   int tx, int ty)
+                                                   int tx, int ty, int kext)
     {
         using LA = TileLayout<T, BM, BK>;
         using LB = TileLayout<T, BN, BK>;
@@ -463,18 +467,18 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                       "fragment chunks must be whole segments apart");
         constexpr int DA = (BM / NCM) / LA::W * LA::SEG, DB = (BN / NCN) / LB::W * LB::SEG;
 #pragma unroll 1
-        for (int k0 = 0; k0 < BK; k0 += UNROLL) {
+        for (int k0 = 0; k0 < kext; k0 += UNROLL) {
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 const int kk = k0 + u;
                 T a[TM], b[TN];
 #pragma unroll
-                for (int c = 0; c < NCM; ++c)
+                for (int c = 0; c < NMA; ++c)
                     lds16<T>(a + c * CH, a0 + c * DA + kk * LA::P);
 #pragma unroll
                 for (int c = 0; c < NCN; ++c)
                     lds16<T>(b + c * CH, b0 + c * DB + kk * LB::P);
-                fma_block(a, b, acc);
+                fma_block<NMA * CH>(a, b, acc);
             }
         }
     }
@@ -482,6 +486,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
     // acc[ii][jj] += a[ii] * b[jj].  FP32 uses the paired FMA of sm_100+ (two lanes of
     // independent single-rounding FMAs per instruction, so the result bits equal fmaf's),
     // which halves the instructions the FFMA-bound loop issues.
+    template <int TME>   // rows of the micro-tile computed (TM, or a fringe tile's first chunks)
     static __device__ __forceinline__ void fma_block(const T (&a)[TM], const T (&b)[TN],
                                                      T (&acc)[TM][TN])
     {
@@ -491,7 +496,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             for (int jj = 0; jj < TN; ++jj) {
                 const float2 bb = make_float2(b[jj], b[jj]);
 #pragma unroll
-                for (int ii = 0; ii < TM; ii += 2) {
+                for (int ii = 0; ii < TME; ii += 2) {
                     const float2 c = __ffma2_rn(make_float2(a[ii], a[ii + 1]), bb,
                                                 make_float2(acc[ii][jj], acc[ii + 1][jj]));
                     acc[ii][jj] = c.x;
@@ -501,7 +506,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         } else if constexpr (std::is_same<T, float>::value) {
             // pairs along n: a[ii] x {b[jj], b[jj+1]}
 #pragma unroll
-            for (int ii = 0; ii < TM; ++ii) {
+            for (int ii = 0; ii < TME; ++ii) {
                 const float2 aa = make_float2(a[ii], a[ii]);
 #pragma unroll
                 for (int jj = 0; jj < TN; jj += 2) {
@@ -513,7 +518,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             }
         } else {
 #pragma unroll
-            for (int ii = 0; ii < TM; ++ii)
+            for (int ii = 0; ii < TME; ++ii)
 #pragma unroll
                 for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fma(a[ii], b[jj], acc[ii][jj]);
         }
@@ -532,12 +537,19 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
 
     // Accumulates op(A)[tile rows, kb0*BK : kb1*BK] * op(B)[..., tile cols] into acc, packing
     // operand tiles on the way where this tile is a producer.
+    // HALF_ROWS: also compile the half-height micro-tile for tiles whose lower row chunks lie
+    // past m (worth its extra code only where most tiles are fringe tiles: grouped problems).
+    template <bool HALF_ROWS = false>
     static __device__ void run_segment(const GemmParams<T> &p, Smem &sm, int i, int j,
                                        int kb0, int kb1, T (&acc)[TM][TN], unsigned int epoch)
     {
         const int tid = threadIdx.x;
         const int tx = tid % TX, ty = tid / TX;
         const int nkb = kb1 - kb0;
+        // fringe tiles: a warp whose columns all lie past n has nothing to compute; if every
+        // row chunk but the first lies past m, only the first is computed
+        const bool warp_idle = j * BN + ((tid & ~31) / TX) * CH >= p.n;
+        const bool half_rows = i * BM + BM / NCM >= p.m;
 
 #pragma unroll
         for (int ii = 0; ii < TM; ++ii)
@@ -601,7 +613,15 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             const bool ahead = (tid == 0) && (it + STAGES < nkb);
             Words w{0ull, 0ull};
             if (ahead) w = fetch_words(p, sm, i, j, kb0 + it + STAGES);
-            compute(sm.a[stage], sm.b[stage], acc, tx, ty);
+            if (!warp_idle) {
+                // the tile's last k-block computes only its rows of k that exist
+                const int kin = p.k - (kb0 + it) * BK;
+                const int kext = kin >= BK ? BK : ((kin + UNROLL - 1) / UNROLL) * UNROLL;
+                if (HALF_ROWS && half_rows)
+                    compute<1>(sm.a[stage], sm.b[stage], acc, tx, ty, kext);
+                else
+                    compute<NCM>(sm.a[stage], sm.b[stage], acc, tx, ty, kext);
+            }
             if (tid == 0) {
                 if (ahead && store_decisions(p, sm, i, j, w, it + STAGES, epoch)) fence_acquire();
                 // the pack stores of the previous k-block were ordered by this iteration's
