@@ -146,11 +146,14 @@ def barrier(world):
 
 
 def max_over_ranks(world, v: float) -> float:
+    """The largest v over the ranks (the slowest rank's time); a CUDA tensor on NCCL, a host
+    tensor on other backends."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
