@@ -175,6 +175,27 @@ int gfip_dsyrk(gfip_handle_t handle, char uplo, char trans, int64_t n, int64_t k
 int gfip_ssyrk(gfip_handle_t handle, char uplo, char trans, int64_t n, int64_t k, float alpha,
                const float *A, int64_t lda, float beta, float *C, int64_t ldc);
 
+/* ---- TRMM on the fused kernel (one of the other level-3 operations, Sec. 1 and Sec. 5) ----
+ *
+ * B := alpha * op(A) * B   (side 'L', A is m x m, lda >= max(1, m))
+ * B := alpha * B * op(A)   (side 'R', A is n x n, lda >= max(1, n))
+ * with B m x n column-major (ldb >= max(1, m)), op(A) = A ('N') or A^T ('T', 'C'), A
+ * triangular: only its uplo triangle ('L' or 'U') is read, and with diag 'U' its diagonal is
+ * not read either and taken as 1.  The product runs on the fused kernel with op(A) read
+ * through a triangular mask: k-blocks outside the triangle are skipped, blocks the diagonal
+ * cuts are masked as they are staged, so the first tile line packs masked panels.  It is
+ * formed out of place in the workspace and copied back into B (rows m..ldb-1 untouched).
+ * BLAS rules: alpha == 0 sets B to zero without reading A or B; m == 0 or n == 0 returns at
+ * once.  Errors: -1 side, -2 uplo, -3 transa, -4 diag, -5 m < 0, -6 n < 0, -9 lda, -11 ldb
+ * (reference-BLAS positions), or a GFIP_ERR_* code.  Needs gfip_trmm_workspace_size() bytes
+ * of workspace; asynchronous on the handle's stream. */
+size_t gfip_trmm_workspace_size(gfip_handle_t handle, char side, char uplo, char transa,
+                                char diag, int64_t m, int64_t n, int elem_bytes);
+int gfip_dtrmm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, double alpha, const double *A, int64_t lda, double *B, int64_t ldb);
+int gfip_strmm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, float alpha, const float *A, int64_t lda, float *B, int64_t ldb);
+
 /* Test hook for the failure path of gfip_dgemm_ozaki (no counterpart in the paper; the
  * paper's CPU kernels have no waits).  Sets, for this handle's later gfip_dgemm_ozaki calls,
  * the budget of every pipeline wait in nanoseconds (0 restores the default, 2 s), and with

@@ -226,7 +226,7 @@ bool too_big(int64_t v)
 template <typename T>
 int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t m, int64_t n,
                 int64_t k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb, T beta,
-                T *C, int64_t ldc);
+                T *C, int64_t ldc, int tmask_a = 0, int tmask_b = 0);
 
 template <typename T>
 int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_t m, int64_t n,
@@ -261,7 +261,7 @@ int gemm_entry(gfip_handle_t handle, Variant v, char transa, char transb, int64_
 template <typename T>
 int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t m, int64_t n,
                 int64_t k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb, T beta,
-                T *C, int64_t ldc)
+                T *C, int64_t ldc, int tmask_a, int tmask_b)
 {
     Plan<T> pl = make_plan<T>(h, v, (int)m, (int)n, (int)k, tri);
     if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
@@ -309,6 +309,8 @@ int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t
     // the upper one, whose first tile line is the first tile row (B's producers)
     p.a_produces = (tri != gfip::TRI_UPPER) ? 1 : 0;
     p.b_produces = (tri == gfip::TRI_NONE || tri == gfip::TRI_UPPER) ? 1 : 0;
+    p.tmask_a = tmask_a;
+    p.tmask_b = tmask_b;
     p.state_a = reinterpret_cast<unsigned long long *>(h->ws + pl.off_state_a);
     p.state_b = reinterpret_cast<unsigned long long *>(h->ws + pl.off_state_b);
     p.tile_count = reinterpret_cast<unsigned long long *>(h->ws + pl.off_count);
@@ -454,6 +456,98 @@ size_t syrk_workspace_impl(Handle *h, char uplo, char trans, int64_t n, int64_t 
     return total_bytes(h, pl);
 }
 
+// Reference-BLAS dtrmm argument check: 0, or minus the 1-based position of the first bad
+// argument in (side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb).
+int check_trmm(char side, char uplo, char transa, char diag, int64_t m, int64_t n, int64_t lda,
+               int64_t ldb)
+{
+    const bool left = side == 'L' || side == 'l';
+    if (!left && side != 'R' && side != 'r') return -1;
+    if (uplo != 'L' && uplo != 'l' && uplo != 'U' && uplo != 'u') return -2;
+    if (!is_notrans(transa) && transa != 'T' && transa != 't' && transa != 'C' &&
+        transa != 'c')
+        return -3;
+    if (diag != 'U' && diag != 'u' && diag != 'N' && diag != 'n') return -4;
+    if (m < 0) return -5;
+    if (n < 0) return -6;
+    if (lda < std::max<int64_t>(1, left ? m : n)) return -9;
+    if (ldb < std::max<int64_t>(1, m)) return -11;
+    return 0;
+}
+
+// The triangle mask of op(A) in the operand role TRMM gives it (see gfip::TriMask): the
+// A role of side 'L' (x = row i, k = p: lower op(A) keeps i >= p), the B role of side 'R'
+// (x = column j, k = p: lower op(A) keeps p >= j); a unit diagonal makes it strict.
+int trmm_mask(char side, char uplo, char transa, char diag)
+{
+    const bool left = side == 'L' || side == 'l';
+    const bool lower_op = (uplo == 'L' || uplo == 'l') != !is_notrans(transa);
+    int mask = gfip::TMASK_ON;
+    if (diag == 'U' || diag == 'u') mask |= gfip::TMASK_STRICT;
+    if (left ? lower_op : !lower_op) mask |= gfip::TMASK_KEEP_GE;
+    return mask;
+}
+
+template <typename T>
+size_t trmm_workspace_impl(Handle *h, char side, int64_t m, int64_t n)
+{
+    const bool left = side == 'L' || side == 'l';
+    const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)m, (int)n, (int)(left ? m : n));
+    return round_up(total_bytes(h, pl), kAlign) + round_up((size_t)m * n * sizeof(T), kAlign);
+}
+
+// TRMM on the fused kernel: W := alpha op(A) B (or alpha B op(A)) with op(A) read through a
+// triangular mask (blocks outside the triangle skipped, blocks on the diagonal masked as
+// they are staged, so the producers pack masked panels), a unit diagonal added as beta =
+// alpha on a copy of B in W; then B := W.  W lives in the workspace after the GEMM's part.
+template <typename T>
+int trmm_entry(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, T alpha, const T *A, int64_t lda, T *B, int64_t ldb)
+{
+    const int info = check_trmm(side, uplo, transa, diag, m, n, lda, ldb);
+    if (info != 0) return info;
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    h->last_launches = 0;
+    h->last_grid = 0;
+    if (m == 0 || n == 0) return GFIP_OK;
+    if (too_big(m) || too_big(n) || too_big(lda) || too_big(ldb)) return GFIP_ERR_SIZE;
+    if (B == nullptr) return GFIP_ERR_NULLPTR;
+    if (alpha == T(0)) {   // B := 0, neither A nor B read
+        if (gfip::launch_scale<T>(B, ldb, (int)m, (int)n, T(0), gfip::TRI_NONE, h->stream) !=
+            cudaSuccess)
+            return GFIP_ERR_CUDA;
+        h->last_launches = 1;
+        return GFIP_OK;
+    }
+    if (A == nullptr) return GFIP_ERR_NULLPTR;
+    if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
+    const bool left = side == 'L' || side == 'l';
+    const bool unit = diag == 'U' || diag == 'u';
+    const int64_t kdim = left ? m : n;
+    const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)m, (int)n, (int)kdim);
+    const size_t w_off = round_up(total_bytes(h, pl), kAlign);
+    const size_t w_bytes = (size_t)m * n * sizeof(T);
+    if (w_off + w_bytes > h->ws_bytes) return GFIP_ERR_WORKSPACE;
+    T *W = reinterpret_cast<T *>(h->ws + w_off);
+    const size_t row_bytes = (size_t)m * sizeof(T);
+    if (unit && cudaMemcpy2DAsync(W, row_bytes, B, (size_t)ldb * sizeof(T), row_bytes, (size_t)n,
+                                  cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        return GFIP_ERR_CUDA;
+    const T beta = unit ? alpha : T(0);
+    const int mask = trmm_mask(side, uplo, transa, diag);
+    const char ta = is_notrans(transa) ? 'N' : 'T';
+    const int rc = left ? launch_plan<T>(h, Variant::Fused, gfip::TRI_NONE, ta, 'N', m, n, m,
+                                         alpha, A, lda, B, ldb, beta, W, m, mask, 0)
+                        : launch_plan<T>(h, Variant::Fused, gfip::TRI_NONE, 'N', ta, m, n, n,
+                                         alpha, B, ldb, A, lda, beta, W, m, 0, mask);
+    if (rc != GFIP_OK) return rc;
+    if (cudaMemcpy2DAsync(B, (size_t)ldb * sizeof(T), W, row_bytes, row_bytes, (size_t)n,
+                          cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        return GFIP_ERR_CUDA;
+    return GFIP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -570,6 +664,34 @@ int gfip_ssyrk(gfip_handle_t handle, char uplo, char trans, int64_t n, int64_t k
                const float *A, int64_t lda, float beta, float *C, int64_t ldc)
 {
     return syrk_entry<float>(handle, uplo, trans, n, k, alpha, A, lda, beta, C, ldc);
+}
+
+size_t gfip_trmm_workspace_size(gfip_handle_t handle, char side, char uplo, char transa,
+                                char diag, int64_t m, int64_t n, int elem_bytes)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return 0;
+    const bool left = side == 'L' || side == 'l';
+    if (check_trmm(side, uplo, transa, diag, m, n, std::max<int64_t>(1, left ? m : n),
+                   std::max<int64_t>(1, m)) != 0)
+        return 0;
+    if (too_big(m) || too_big(n)) return 0;
+    if (m == 0 || n == 0) return round_up(kHeader, kCtrlGranule);
+    if (elem_bytes == 8) return trmm_workspace_impl<double>(h, side, m, n);
+    if (elem_bytes == 4) return trmm_workspace_impl<float>(h, side, m, n);
+    return 0;
+}
+
+int gfip_dtrmm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, double alpha, const double *A, int64_t lda, double *B, int64_t ldb)
+{
+    return trmm_entry<double>(handle, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb);
+}
+
+int gfip_strmm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, float alpha, const float *A, int64_t lda, float *B, int64_t ldb)
+{
+    return trmm_entry<float>(handle, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb);
 }
 
 int gfip_dgemm(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n, int64_t k,

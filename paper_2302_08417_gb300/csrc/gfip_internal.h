@@ -11,6 +11,11 @@ namespace gfip {
 // Part of C a launch computes: all of it (GEMM), or one triangle of a square C (SYRK).
 enum Triangle : int { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
 
+// Triangular operand (TRMM): element (x, k) of op(X) (x = row of op(A) or column of op(B),
+// k = the summed index) is kept when x - k >= s (KEEP_GE) or k - x >= s, s = 1 for a strictly
+// triangular operand (a unit diagonal is added separately), else s = 0; the rest is zero.
+enum TriMask : int { TMASK_ON = 1, TMASK_KEEP_GE = 2, TMASK_STRICT = 4 };
+
 enum OperandMode : int {
     MODE_RAW = 0,     // always read the raw strided operand (direct variant, SUP analog)
     MODE_PACKED = 1,  // always read the packed copy, written beforehand by the pack kernel
@@ -93,6 +98,8 @@ template <typename T> struct GemmParams {
     int tri;          // TRI_NONE: all of C; TRI_LOWER / TRI_UPPER: that triangle (SYRK)
     int a_produces;   // the first tile column packs the A panels
     int b_produces;   // the first tile row packs the B panels
+    int tmask_a;      // triangular mask of op(A) (TRMM), 0 = dense; see TriMask
+    int tmask_b;      // triangular mask of op(B)
     int grid;         // persistent CTAs
     int dp_tiles;     // tiles [0, dp_tiles) are data-parallel: tile t runs on CTA t % grid
     int64_t sk_iters; // (tiles - dp_tiles) * kt iterations split evenly over the CTAs

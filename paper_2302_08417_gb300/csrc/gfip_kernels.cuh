@@ -37,7 +37,25 @@ namespace gfip {
 
 constexpr unsigned int STATUS_BAD_SEGMENT = 0x1u;  // mirrors GFIP_STATUS_BAD_SEGMENT
 
-enum Decision : int { DEC_RAW = 0, DEC_PACKED = 1, DEC_PRODUCE = 2 };
+enum Decision : int { DEC_RAW = 0, DEC_PACKED = 1, DEC_PRODUCE = 2, DEC_SKIP = 3 };
+
+__device__ __forceinline__ bool tmask_keep(int mask, int x, int k)
+{
+    const int s = (mask & TMASK_STRICT) ? 1 : 0;
+    return (mask & TMASK_KEEP_GE) ? (x - k >= s) : (k - x >= s);
+}
+
+// A BX x BK operand block at (x0, k0) under a mask: 0 all kept, 1 partly kept, 2 all zero.
+__device__ __forceinline__ int tmask_class(int mask, int x0, int bx, int k0, int bk)
+{
+    if (!(mask & TMASK_ON)) return 0;
+    const int s = (mask & TMASK_STRICT) ? 1 : 0;
+    const int lo = (mask & TMASK_KEEP_GE) ? x0 - (k0 + bk - 1) : k0 - (x0 + bx - 1);
+    const int hi = (mask & TMASK_KEEP_GE) ? (x0 + bx - 1) - k0 : (k0 + bk - 1) - x0;
+    if (lo >= s) return 0;
+    if (hi < s) return 2;
+    return 1;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -126,6 +144,7 @@ template <typename T, int BX, int BK, int THREADS, bool CONTIG> struct RawLoader
     const T *g;       // operand base (a valid address for zero-filled copies)
     const T *p;       // this thread's element 0 at the next k-block to issue
     int64_t ld;
+    int xg;           // global x of element 0 (for triangular masks)
     uint32_t xok;     // bit GX(r): x of element r lies inside the operand (CONTIG: bit 0 only)
     int kk0;          // kk of element 0
     uint32_t s0;      // shared-memory byte offset (within a stage) of element 0
@@ -138,6 +157,7 @@ template <typename T, int BX, int BK, int THREADS, bool CONTIG> struct RawLoader
         if (CONTIG) {
             const int x = tid % BX;
             kk0 = tid / BX;
+            xg = x0 + x;
             p = g + (int64_t)(x0 + x) + (int64_t)(k0 + kk0) * ld;
             xok = (x0 + x < x_ext) ? 1u : 0u;
             s0 = 0;
@@ -145,6 +165,7 @@ template <typename T, int BX, int BK, int THREADS, bool CONTIG> struct RawLoader
             const int lane = tid & 31, w = tid >> 5;
             const int x = 4 * w + (lane >> 3);
             kk0 = lane & 7;
+            xg = x0 + x;
             p = g + (int64_t)(k0 + kk0) + (int64_t)(x0 + x) * ld;
             xok = 0;
 #pragma unroll
@@ -176,6 +197,35 @@ template <typename T, int BX, int BK, int THREADS, bool CONTIG> struct RawLoader
                 // x and x + DX(r) lie in the same 128-byte column position when DX(r) is a
                 // multiple of W, or DX(r) < W apart in the same segment: either way the
                 // layout offset moves by a constant
+                const uint32_t soff =
+                    s0 + ((DX(r) / L::W) * L::SEG + (DX(r) % L::W) + DK(r) * L::P) * sizeof(T);
+                cp_async_elem<sizeof(T)>(sdst + soff, src, ok);
+            }
+            p += BK;
+        }
+    }
+
+    // issue() for a block that a triangular mask cuts: elements outside the triangle are
+    // zero-filled, not read (kstart = k of the block's first row).
+    __device__ __forceinline__ void issue_masked(uint32_t sdst, int kleft, int kstart, int mask,
+                                                 int tid)
+    {
+        if (CONTIG) {
+            const int x = tid % BX;
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int kk = kk0 + r * (THREADS / BX);
+                const bool ok = xok && (kk < kleft) && tmask_keep(mask, xg, kstart + kk);
+                const T *src = ok ? p + (int64_t)(r * (THREADS / BX)) * ld : g;
+                cp_async_elem<sizeof(T)>(sdst + L::off(x, kk) * sizeof(T), src, ok);
+            }
+            p += (int64_t)BK * ld;
+        } else {
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const bool ok = ((xok >> GX(r)) & 1u) && (kk0 + DK(r) < kleft) &&
+                                tmask_keep(mask, xg + DX(r), kstart + kk0 + DK(r));
+                const T *src = ok ? p + (int64_t)DX(r) * ld + DK(r) : g;
                 const uint32_t soff =
                     s0 + ((DX(r) / L::W) * L::SEG + (DX(r) % L::W) + DK(r) * L::P) * sizeof(T);
                 cp_async_elem<sizeof(T)>(sdst + soff, src, ok);
@@ -317,6 +367,7 @@ template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     T b[Cfg::STAGES][TileLayout<T, Cfg::BN, Cfg::BK>::ELEMS];
     int dec_a[2 * Cfg::STAGES];
     int dec_b[2 * Cfg::STAGES];
+    int part[2 * Cfg::STAGES];   // bit 0 (1): the A (B) block is cut by a triangular mask
     int full_a, full_b;  // the tile's whole A (B) panel is already published
     int flag;
 };
@@ -413,11 +464,22 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
     // Stores the decisions for local k-block q; returns true if one of them reads a tile
     // published by another CTA (the caller then issues fence_acquire()).
     static __device__ __forceinline__ bool store_decisions(const GemmParams<T> &p,
-                                                           Smem &sm, int i, int j,
+                                                           Smem &sm, int i, int j, int kb,
                                                            Words w, int q, unsigned int epoch)
     {
-        const int da = classify(p.mode_a, prod_a(p, j), sm.full_a, w.a, epoch);
-        const int db = classify(p.mode_b, prod_b(p, i), sm.full_b, w.b, epoch);
+        int da = classify(p.mode_a, prod_a(p, j), sm.full_a, w.a, epoch);
+        int db = classify(p.mode_b, prod_b(p, i), sm.full_b, w.b, epoch);
+        // triangular operands: a k-block in which either operand block lies outside its
+        // triangle contributes nothing and is not computed; an operand block is then not
+        // loaded either, unless this tile packs it for others (a producer packs every
+        // nonzero block of its panel, so a panel published complete has no holes); a block
+        // the diagonal cuts is loaded with a mask
+        const int ca = tmask_class(p.tmask_a, i * BM, BM, kb * BK, BK);
+        const int cb = tmask_class(p.tmask_b, j * BN, BN, kb * BK, BK);
+        const bool idle = (ca == 2 || cb == 2);
+        if (ca == 2 || (idle && da != DEC_PRODUCE)) da = DEC_SKIP;
+        if (cb == 2 || (idle && db != DEC_PRODUCE)) db = DEC_SKIP;
+        sm.part[q % DEC] = (ca == 1 ? 1 : 0) | (cb == 1 ? 2 : 0) | (idle ? 4 : 0);
         sm.dec_a[q % DEC] = da;
         sm.dec_b[q % DEC] = db;
         return (da == DEC_PACKED && p.mode_a == MODE_FIP && !sm.full_a) ||
@@ -431,17 +493,26 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         const int stage = q % STAGES;
         const int kleft = p.k - kb * BK;
         const uint32_t sa = smem_addr(sm.a[stage]), sb = smem_addr(sm.b[stage]);
-        if (sm.dec_a[q % DEC] == DEC_PACKED) {
+        const int part = sm.part[q % DEC];
+        if (sm.dec_a[q % DEC] == DEC_SKIP) {
+            la.skip();
+        } else if (sm.dec_a[q % DEC] == DEC_PACKED) {
             load_packed_tile<T, BM, BK, THREADS>(
                 sa, p.pack_a + ((int64_t)i * p.kt + kb) * (BM * BK), tid);
             la.skip();
+        } else if (part & 1) {
+            la.issue_masked(sa, kleft, kb * BK, p.tmask_a, tid);
         } else {
             la.issue(sa, kleft, tid);
         }
-        if (sm.dec_b[q % DEC] == DEC_PACKED) {
+        if (sm.dec_b[q % DEC] == DEC_SKIP) {
+            lb.skip();
+        } else if (sm.dec_b[q % DEC] == DEC_PACKED) {
             load_packed_tile<T, BN, BK, THREADS>(
                 sb, p.pack_b + ((int64_t)j * p.kt + kb) * (BN * BK), tid);
             lb.skip();
+        } else if (part & 2) {
+            lb.issue_masked(sb, kleft, kb * BK, p.tmask_b, tid);
         } else {
             lb.issue(sb, kleft, tid);
         }
@@ -586,7 +657,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             bool acq = fa || fb;
 #pragma unroll
             for (int q = 0; q < STAGES; ++q)
-                if (q < nkb) acq |= store_decisions(p, sm, i, j, w[q], q, epoch);
+                if (q < nkb) acq |= store_decisions(p, sm, i, j, kb0 + q, w[q], q, epoch);
             if (acq) fence_acquire();
         }
         __syncthreads();
@@ -613,7 +684,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             const bool ahead = (tid == 0) && (it + STAGES < nkb);
             Words w{0ull, 0ull};
             if (ahead) w = fetch_words(p, sm, i, j, kb0 + it + STAGES);
-            if (!warp_idle) {
+            if (!warp_idle && !(sm.part[it % DEC] & 4)) {
                 // the tile's last k-block computes only its rows of k that exist
                 const int kin = p.k - (kb0 + it) * BK;
                 const int kext = kin >= BK ? BK : ((kin + UNROLL - 1) / UNROLL) * UNROLL;
@@ -623,7 +694,8 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
                     compute<NCM>(sm.a[stage], sm.b[stage], acc, tx, ty, kext);
             }
             if (tid == 0) {
-                if (ahead && store_decisions(p, sm, i, j, w, it + STAGES, epoch)) fence_acquire();
+                if (ahead && store_decisions(p, sm, i, j, kb0 + it + STAGES, w, it + STAGES, epoch))
+                    fence_acquire();
                 // the pack stores of the previous k-block were ordered by this iteration's
                 // barrier and have drained during the compute
                 if (it > 0) publish_produced(p, sm, i, j, kb0, it - 1, epoch);

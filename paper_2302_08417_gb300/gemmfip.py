@@ -67,6 +67,11 @@ SIGNATURES = {
     "gfip_syrk_workspace_size": (_sz, [_ptr, _chr, _chr, _i64, _i64, _int]),
     "gfip_dsyrk": (_int, [_ptr, _chr, _chr, _i64, _i64, _dbl, _ptr, _i64, _dbl, _ptr, _i64]),
     "gfip_ssyrk": (_int, [_ptr, _chr, _chr, _i64, _i64, _flt, _ptr, _i64, _flt, _ptr, _i64]),
+    "gfip_trmm_workspace_size": (_sz, [_ptr, _chr, _chr, _chr, _chr, _i64, _i64, _int]),
+    "gfip_dtrmm": (_int, [_ptr, _chr, _chr, _chr, _chr, _i64, _i64, _dbl, _ptr, _i64, _ptr,
+                          _i64]),
+    "gfip_strmm": (_int, [_ptr, _chr, _chr, _chr, _chr, _i64, _i64, _flt, _ptr, _i64, _ptr,
+                          _i64]),
 }
 
 _lock = threading.Lock()
@@ -214,6 +219,18 @@ def gfip_syrk(esz, handle, uplo, trans, n, k, alpha, A, lda, beta, C, ldc) -> in
     return fn(handle, _b(uplo), _b(trans), n, k, alpha, A or None, lda, beta, C or None, ldc)
 
 
+def gfip_trmm_workspace_size(handle, side, uplo, transa, diag, m, n, elem_bytes) -> int:
+    return load().gfip_trmm_workspace_size(handle, _b(side), _b(uplo), _b(transa), _b(diag), m,
+                                           n, elem_bytes)
+
+
+def gfip_trmm(esz, handle, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb) -> int:
+    """gfip_dtrmm (esz 8) or gfip_strmm (esz 4); A and B are device pointers."""
+    fn = load().gfip_dtrmm if esz == 8 else load().gfip_strmm
+    return fn(handle, _b(side), _b(uplo), _b(transa), _b(diag), m, n, alpha, A or None, lda,
+              B or None, ldb)
+
+
 def gfip_grouped_workspace_size(handle, count) -> int:
     return load().gfip_grouped_workspace_size(handle, count)
 
@@ -264,6 +281,13 @@ class Handle:
 
     def ensure_syrk_workspace(self, uplo, trans, n, k, elem_bytes):
         need = gfip_syrk_workspace_size(self.h, uplo, trans, n, k, elem_bytes)
+        if self.workspace is None or self.workspace.numel() < need:
+            if self.workspace is not None:
+                self._torch.cuda.current_stream().synchronize()
+            self._set_ws(int(need * 1.25) + (1 << 20))
+
+    def ensure_trmm_workspace(self, side, uplo, transa, diag, m, n, elem_bytes):
+        need = gfip_trmm_workspace_size(self.h, side, uplo, transa, diag, m, n, elem_bytes)
         if self.workspace is None or self.workspace.numel() < need:
             if self.workspace is not None:
                 self._torch.cuda.current_stream().synchronize()
