@@ -20,7 +20,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gemm_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "syrk_oracle.c"), os.path.join(_HERE, "trmm_oracle.c")]
+_SRCS = [_SRC] + [os.path.join(_HERE, f) for f in ("syrk_oracle.c", "trmm_oracle.c",
+                                                     "trsm_oracle.c")]
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -59,6 +60,8 @@ def _load():
             lib.oracle_trmm.argtypes = [ctypes.c_char, ctypes.c_char, ctypes.c_char,
                                         ctypes.c_char, i64, i64, dbl, ptr, i64, ptr, i64]
             lib.oracle_trmm.restype = ctypes.c_int
+            lib.oracle_trsm.argtypes = lib.oracle_trmm.argtypes
+            lib.oracle_trsm.restype = ctypes.c_int
             lib.oracle_max_threads.argtypes = []
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -173,4 +176,22 @@ def trmm_result(side, uplo, transa, diag, m, n, alpha, A, lda, B0, ldb) -> np.nd
     rc = trmm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb)
     if rc != 0:
         raise ValueError(f"oracle_trmm returned {rc}")
+    return B
+
+
+def trsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb) -> int:
+    """In place on B (flat float64, column-major): X with op(A) X = alpha B (side 'L') or
+    X op(A) = alpha B (side 'R'), A triangular.  Returns 0 or minus the reference-BLAS
+    position of the first bad argument."""
+    lib = _load()
+    return lib.oracle_trsm(side.encode(), uplo.encode(), transa.encode(), diag.encode(), m, n,
+                           float(alpha), _ptr(_f64(A, "A")), lda, _ptr(_f64(B, "B")), ldb)
+
+
+def trsm_result(side, uplo, transa, diag, m, n, alpha, A, lda, B0, ldb) -> np.ndarray:
+    """Out-of-place convenience: returns a new flat buffer holding the solution X."""
+    B = np.array(B0, dtype=np.float64, copy=True)
+    rc = trsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb)
+    if rc != 0:
+        raise ValueError(f"oracle_trsm returned {rc}")
     return B
