@@ -196,6 +196,25 @@ int gfip_dtrmm(gfip_handle_t handle, char side, char uplo, char transa, char dia
 int gfip_strmm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
                int64_t n, float alpha, const float *A, int64_t lda, float *B, int64_t ldb);
 
+/* ---- TRSM on the fused kernel (one of the other level-3 operations, Sec. 1 and Sec. 5) ----
+ *
+ * Solves op(A) * X = alpha * B (side 'L', A m x m) or X * op(A) = alpha * B (side 'R',
+ * A n x n) and overwrites B (m x n, column-major, ldb >= max(1, m)) with X; op(A), uplo,
+ * diag and lda as for gfip_dtrmm (only the uplo triangle of A is read, and not its
+ * diagonal for diag 'U').  Blocked: over the diagonal blocks of op(A) (64 unknowns) in solve
+ * order, a substitution kernel solves the block for every right-hand side, then one fused
+ * GEMM (alpha -1, beta 1) removes its contribution from the unknowns still to be solved.
+ * No singularity test is made (as in the reference BLAS): a zero on a non-unit diagonal
+ * gives Inf or NaN.  BLAS rules: alpha == 0 sets B to zero without reading A or B; m == 0
+ * or n == 0 returns at once.  Errors as gfip_dtrmm.  Needs gfip_trsm_workspace_size() bytes
+ * of workspace; asynchronous on the handle's stream (many launches, no host read-back). */
+size_t gfip_trsm_workspace_size(gfip_handle_t handle, char side, char uplo, char transa,
+                                char diag, int64_t m, int64_t n, int elem_bytes);
+int gfip_dtrsm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, double alpha, const double *A, int64_t lda, double *B, int64_t ldb);
+int gfip_strsm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, float alpha, const float *A, int64_t lda, float *B, int64_t ldb);
+
 /* Test hook for the failure path of gfip_dgemm_ozaki (no counterpart in the paper; the
  * paper's CPU kernels have no waits).  Sets, for this handle's later gfip_dgemm_ozaki calls,
  * the budget of every pipeline wait in nanoseconds (0 restores the default, 2 s), and with

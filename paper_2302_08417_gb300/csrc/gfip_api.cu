@@ -548,6 +548,80 @@ int trmm_entry(gfip_handle_t handle, char side, char uplo, char transa, char dia
     return GFIP_OK;
 }
 
+template <typename T>
+size_t trsm_workspace_impl(Handle *h, char side, int64_t m, int64_t n)
+{
+    // the largest update: all of B against one block of TRSM_NB
+    const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)m, (int)n, gfip::TRSM_NB);
+    return total_bytes(h, pl);
+}
+
+// TRSM, blocked: B := alpha B, then over the diagonal blocks of op(A) in solve order
+// (forward for a lower triangular system, backward for an upper one; for side 'R' the system
+// of each row of X is op(A)^T): solve the block's unknowns for every right-hand side
+// (trsm_diag_kernel), then subtract their contribution from the unknowns still to be solved
+// with one fused GEMM (alpha = -1, beta = 1), whose first tile line packs the block's panel
+// of X (and of op(A)) once for all later tiles.  Only the triangle of A is read.
+template <typename T>
+int trsm_entry(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, T alpha, const T *A, int64_t lda, T *B, int64_t ldb)
+{
+    const int info = check_trmm(side, uplo, transa, diag, m, n, lda, ldb);
+    if (info != 0) return info;
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    h->last_launches = 0;
+    h->last_grid = 0;
+    if (m == 0 || n == 0) return GFIP_OK;
+    if (too_big(m) || too_big(n) || too_big(lda) || too_big(ldb)) return GFIP_ERR_SIZE;
+    if (B == nullptr) return GFIP_ERR_NULLPTR;
+    if (alpha != T(1)) {   // B := alpha B (alpha == 0: zeros, B not read)
+        if (gfip::launch_scale<T>(B, ldb, (int)m, (int)n, alpha, gfip::TRI_NONE, h->stream) !=
+            cudaSuccess)
+            return GFIP_ERR_CUDA;
+        if (alpha == T(0)) return GFIP_OK;
+    }
+    if (A == nullptr) return GFIP_ERR_NULLPTR;
+    const bool left = side == 'L' || side == 'l';
+    const bool trans = !is_notrans(transa);
+    const bool lower_op = (uplo == 'L' || uplo == 'l') != trans;
+    const bool lower_t = left ? lower_op : !lower_op;
+    const bool unit = diag == 'U' || diag == 'u';
+    const int na = (int)(left ? m : n);
+    const int nblocks = (na + gfip::TRSM_NB - 1) / gfip::TRSM_NB;
+    const char ta = trans ? 'T' : 'N';
+    for (int step = 0; step < nblocks; ++step) {
+        const int kbi = lower_t ? step : nblocks - 1 - step;
+        const int k0 = kbi * gfip::TRSM_NB;
+        const int kb = std::min(gfip::TRSM_NB, na - k0);
+        // the block's unknowns: rows k0.. of B (side L) or its columns k0.. (side R)
+        cudaError_t e = left ? gfip::launch_trsm_diag<T>(B + k0, ldb, 1, (int)n, A, lda, trans,
+                                                         k0, kb, lower_t, 0, unit, h->stream)
+                             : gfip::launch_trsm_diag<T>(B + (int64_t)k0 * ldb, 1, ldb, (int)m,
+                                                         A, lda, trans, k0, kb, lower_t, 1, unit,
+                                                         h->stream);
+        if (e != cudaSuccess) return GFIP_ERR_CUDA;
+        // the unknowns still to be solved: after the block (forward) or before it (backward)
+        const int r0 = lower_t ? k0 + kb : 0, r1 = lower_t ? na : k0;
+        if (r1 <= r0) continue;
+        int rc;
+        if (left) {
+            // B[r0:r1, :] -= op(A)[r0:r1, k0:k0+kb] * X[k0:k0+kb, :]
+            const T *ap = trans ? A + k0 + (int64_t)r0 * lda : A + r0 + (int64_t)k0 * lda;
+            rc = launch_plan<T>(h, Variant::Fused, gfip::TRI_NONE, ta, 'N', r1 - r0, n, kb,
+                                T(-1), ap, lda, B + k0, ldb, T(1), B + r0, ldb);
+        } else {
+            // B[:, r0:r1] -= X[:, k0:k0+kb] * op(A)[k0:k0+kb, r0:r1]
+            const T *ap = trans ? A + r0 + (int64_t)k0 * lda : A + k0 + (int64_t)r0 * lda;
+            rc = launch_plan<T>(h, Variant::Fused, gfip::TRI_NONE, 'N', ta, m, r1 - r0, kb,
+                                T(-1), B + (int64_t)k0 * ldb, ldb, ap, lda, T(1),
+                                B + (int64_t)r0 * ldb, ldb);
+        }
+        if (rc != GFIP_OK) return rc;
+    }
+    return GFIP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -692,6 +766,34 @@ int gfip_strmm(gfip_handle_t handle, char side, char uplo, char transa, char dia
                int64_t n, float alpha, const float *A, int64_t lda, float *B, int64_t ldb)
 {
     return trmm_entry<float>(handle, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb);
+}
+
+size_t gfip_trsm_workspace_size(gfip_handle_t handle, char side, char uplo, char transa,
+                                char diag, int64_t m, int64_t n, int elem_bytes)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return 0;
+    const bool left = side == 'L' || side == 'l';
+    if (check_trmm(side, uplo, transa, diag, m, n, std::max<int64_t>(1, left ? m : n),
+                   std::max<int64_t>(1, m)) != 0)
+        return 0;
+    if (too_big(m) || too_big(n)) return 0;
+    if (m == 0 || n == 0) return round_up(kHeader, kCtrlGranule);
+    if (elem_bytes == 8) return trsm_workspace_impl<double>(h, side, m, n);
+    if (elem_bytes == 4) return trsm_workspace_impl<float>(h, side, m, n);
+    return 0;
+}
+
+int gfip_dtrsm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, double alpha, const double *A, int64_t lda, double *B, int64_t ldb)
+{
+    return trsm_entry<double>(handle, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb);
+}
+
+int gfip_strsm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
+               int64_t n, float alpha, const float *A, int64_t lda, float *B, int64_t ldb)
+{
+    return trsm_entry<float>(handle, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb);
 }
 
 int gfip_dgemm(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n, int64_t k,

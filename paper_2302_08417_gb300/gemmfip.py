@@ -72,6 +72,11 @@ SIGNATURES = {
                           _i64]),
     "gfip_strmm": (_int, [_ptr, _chr, _chr, _chr, _chr, _i64, _i64, _flt, _ptr, _i64, _ptr,
                           _i64]),
+    "gfip_trsm_workspace_size": (_sz, [_ptr, _chr, _chr, _chr, _chr, _i64, _i64, _int]),
+    "gfip_dtrsm": (_int, [_ptr, _chr, _chr, _chr, _chr, _i64, _i64, _dbl, _ptr, _i64, _ptr,
+                          _i64]),
+    "gfip_strsm": (_int, [_ptr, _chr, _chr, _chr, _chr, _i64, _i64, _flt, _ptr, _i64, _ptr,
+                          _i64]),
 }
 
 _lock = threading.Lock()
@@ -231,6 +236,18 @@ def gfip_trmm(esz, handle, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb
               B or None, ldb)
 
 
+def gfip_trsm_workspace_size(handle, side, uplo, transa, diag, m, n, elem_bytes) -> int:
+    return load().gfip_trsm_workspace_size(handle, _b(side), _b(uplo), _b(transa), _b(diag), m,
+                                           n, elem_bytes)
+
+
+def gfip_trsm(esz, handle, side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb) -> int:
+    """gfip_dtrsm (esz 8) or gfip_strsm (esz 4); A and B are device pointers."""
+    fn = load().gfip_dtrsm if esz == 8 else load().gfip_strsm
+    return fn(handle, _b(side), _b(uplo), _b(transa), _b(diag), m, n, alpha, A or None, lda,
+              B or None, ldb)
+
+
 def gfip_grouped_workspace_size(handle, count) -> int:
     return load().gfip_grouped_workspace_size(handle, count)
 
@@ -288,6 +305,13 @@ class Handle:
 
     def ensure_trmm_workspace(self, side, uplo, transa, diag, m, n, elem_bytes):
         need = gfip_trmm_workspace_size(self.h, side, uplo, transa, diag, m, n, elem_bytes)
+        if self.workspace is None or self.workspace.numel() < need:
+            if self.workspace is not None:
+                self._torch.cuda.current_stream().synchronize()
+            self._set_ws(int(need * 1.25) + (1 << 20))
+
+    def ensure_trsm_workspace(self, side, uplo, transa, diag, m, n, elem_bytes):
+        need = gfip_trsm_workspace_size(self.h, side, uplo, transa, diag, m, n, elem_bytes)
         if self.workspace is None or self.workspace.numel() < need:
             if self.workspace is not None:
                 self._torch.cuda.current_stream().synchronize()
