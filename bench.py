@@ -729,6 +729,71 @@ def trmm_report(g, torch, shapes=((8192, 8192), (2048, 2048))):
     return out
 
 
+def trsm_report(g, torch, shapes=((8192, 8192), (2048, 2048))):
+    """TRSM (side L, lower, 'N', non-unit, ld = m + 7; a well-conditioned system: off-diagonal
+    entries U[-1, 1] / m, diagonal 2) on the fused kernel: GFLOP/s counted as m^2 n (the
+    substitution's multiply-adds), fused and raw-only, against the full GEMM of the same
+    shape.  Device time of one whole solve (a diagonal solve and a GEMM update per 64-wide
+    block), CUDA events, best of a few."""
+    out = {"note": "side L, uplo L, trans N, diag N, ld = m + 7; flops m^2 n; blocks of 64"}
+    h = g.Handle()
+    h.bind_stream()
+    for dtype, tag in ((torch.float64, "f64"), (torch.float32, "f32")):
+        esz = 8 if tag == "f64" else 4
+        rows = {}
+        for m, n in shapes:
+            A, B, C = make_operands(m + n + 1, dtype, m, n, m)
+            A.mul_(1.0 / m)
+            A.diagonal().fill_(2.0)
+            B0 = B.clone()   # a dense copy (its own layout): only ever copied back into B
+            lda, ldb = A.stride(1), B.stride(1)
+            h.ensure_trsm_workspace("L", "L", "N", "N", m, n, esz)
+            h.ensure_workspace("N", "N", m, n, m, esz)
+
+            def best(fn, reps):
+                t = float("inf")
+                for _ in range(reps + 1):
+                    B.copy_(B0)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    fn()
+                    e1.record()
+                    e1.synchronize()
+                    t = min(t, e0.elapsed_time(e1))
+                return t
+            reps = 2 if m * m * n > 2 ** 36 else 5
+            r = {}
+            for pol, name in ((g.GFIP_PACK_AUTO, "fused"), (g.GFIP_PACK_NONE, "raw_only")):
+                h.set_pack_policy(pol)
+
+                def call():
+                    rc = g.gfip_trsm(esz, h.h, "L", "L", "N", "N", m, n, 1.0, A.data_ptr(), lda,
+                                     B.data_ptr(), ldb)
+                    assert rc == 0, rc
+                ms = best(call, reps)
+                r[name] = round(m * m * n / 1e9 / (ms * 1e-3), 1)
+                r[name + "_ms"] = round(ms, 3)
+            h.set_pack_policy(g.GFIP_PACK_AUTO)
+            gname = g.ENTRY[("fused", esz)]
+
+            def gcall():
+                rc = g._gemm_call(gname, h.h, "N", "N", m, n, m, 1.0, A.data_ptr(), lda,
+                                  B.data_ptr(), ldb, 0.0, C.data_ptr(), C.stride(1))
+                assert rc == 0, rc
+            gms = best(gcall, reps)
+            r["gemm_ms"] = round(gms, 3)
+            r["trsm_time_over_gemm"] = round(r["fused_ms"] / gms, 3)
+            peak = FP64_PEAK_GFLOPS if tag == "f64" else FP32_PEAK_GFLOPS
+            r["fused_frac_of_peak"] = round(r["fused"] / peak, 4)
+            rows[f"{m}x{n}"] = r
+            del A, B, B0, C
+        out[tag] = rows
+    out["status"] = h.status()
+    return out
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -801,8 +866,9 @@ def main():
     ap.add_argument("--autograd-only", action="store_true",
                     help="only run the differentiable-GEMM report")
     ap.add_argument("--syrk-only", action="store_true",
-                    help="only run the SYRK and TRMM reports")
-    ap.add_argument("--no-syrk", action="store_true", help="skip the SYRK and TRMM reports")
+                    help="only run the SYRK, TRMM and TRSM reports")
+    ap.add_argument("--no-syrk", action="store_true",
+                    help="skip the SYRK, TRMM and TRSM reports")
     ap.add_argument("--no-autograd", action="store_true")
     args = ap.parse_args()
     if args.size != M or args.dtype != "f64" or args.variant != "fused":
@@ -832,6 +898,7 @@ def main():
         if args.syrk_only:
             out["syrk"] = syrk_report(g, torch)
             out["trmm"] = trmm_report(g, torch)
+            out["trsm"] = trsm_report(g, torch)
         if args.autograd_only:
             out["autograd"] = autograd_report(torch)
         if args.emulation_only:
@@ -963,6 +1030,7 @@ def main():
     if rank == 0 and not args.no_syrk:
         result["syrk"] = syrk_report(g, torch)
         result["trmm"] = trmm_report(g, torch)
+        result["trsm"] = trsm_report(g, torch)
     if rank == 0 and not args.no_spectrum:
         result["spectrum_gflops"] = spectrum(h, g, torch)
         result["spectrum_gflops"]["note"] = ("N/N, ld = m + 7, beta = 0.5, best of a few "
