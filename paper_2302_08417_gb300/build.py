@@ -19,8 +19,8 @@ LIB = os.path.join(OUT, "libgemmfip.so")
 PROBE = os.path.join(OUT, "peak_probe")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-LIB_SOURCES = ["gfip_api.cu", "gfip_f64.cu", "gfip_f32.cu", "gfip_ozaki.cu", "gfip_grouped.cu",
-               "gfip_trsm.cu"]
+LIB_SOURCES = ["gfip_api.cu", "gfip_f64.cu", "gfip_f32.cu", "gfip_f64_tmask.cu",
+               "gfip_f32_tmask.cu", "gfip_ozaki.cu", "gfip_grouped.cu", "gfip_trsm.cu"]
 HEADERS = ["gfip_internal.h", "gfip_kernels.cuh", "gfip_grouped.h"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-I" + os.path.join(ROOT, "include")]

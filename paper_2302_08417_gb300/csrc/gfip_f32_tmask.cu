@@ -1,0 +1,4 @@
+// FP32 GEMM kernels with triangular-operand masks (TRMM), compiled apart from the others.
+#include "gfip_kernels.cuh"
+
+GFIP_TMASK_LAUNCHERS(, float)

@@ -119,10 +119,10 @@ __device__ __forceinline__ void grouped_tile(const GroupDesc<T> &d, GemmSmem<T, 
     p.mode_a = MODE_RAW;
     p.mode_b = MODE_RAW;
     typename K::AccT acc;
-    // the half-height micro-tile pays where the pipe is the bound and registers allow it:
-    // FP64 (DFMA-bound) and the 64-thread FP32 tile, not the 128-register FP32 tile
-    constexpr bool HALF_ROWS = std::is_same<T, double>::value || Cfg::THREADS <= 64;
-    K::template run_segment<HALF_ROWS>(p, sm, i, j, 0, d.kt, acc, 0u);
+    // fringe shortcuts for every grouped tile; the half-height micro-tile only where the
+    // registers allow it (FP64, the 64-thread FP32 tile), not in the 128-register FP32 tile
+    constexpr int FRINGE = (std::is_same<T, double>::value || Cfg::THREADS <= 64) ? 2 : 1;
+    K::template run_segment<FRINGE>(p, sm, i, j, 0, d.kt, acc, 0u);
     K::epilogue(p, i, j, acc);
 }
 

@@ -389,7 +389,9 @@ template <> __device__ __forceinline__ void lds16<float>(float *dst, const float
     dst[3] = v.w;
 }
 
-template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struct Kernel {
+// TMASK: compile the triangular-operand handling (TRMM); every other launch runs without it.
+template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>, bool TMASK = false>
+struct Kernel {
     using Cfg = C;
     using Smem = GemmSmem<T, C>;
     static constexpr int BM = Cfg::BM, BN = Cfg::BN, BK = Cfg::BK;
@@ -469,17 +471,21 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
     {
         int da = classify(p.mode_a, prod_a(p, j), sm.full_a, w.a, epoch);
         int db = classify(p.mode_b, prod_b(p, i), sm.full_b, w.b, epoch);
-        // triangular operands: a k-block in which either operand block lies outside its
-        // triangle contributes nothing and is not computed; an operand block is then not
-        // loaded either, unless this tile packs it for others (a producer packs every
-        // nonzero block of its panel, so a panel published complete has no holes); a block
-        // the diagonal cuts is loaded with a mask
-        const int ca = tmask_class(p.tmask_a, i * BM, BM, kb * BK, BK);
-        const int cb = tmask_class(p.tmask_b, j * BN, BN, kb * BK, BK);
-        const bool idle = (ca == 2 || cb == 2);
-        if (ca == 2 || (idle && da != DEC_PRODUCE)) da = DEC_SKIP;
-        if (cb == 2 || (idle && db != DEC_PRODUCE)) db = DEC_SKIP;
-        sm.part[q % DEC] = (ca == 1 ? 1 : 0) | (cb == 1 ? 2 : 0) | (idle ? 4 : 0);
+        if constexpr (TMASK) {
+            // triangular operands: a k-block in which either operand block lies outside its
+            // triangle contributes nothing and is not computed; an operand block is then not
+            // loaded either, unless this tile packs it for others (a producer packs every
+            // nonzero block of its panel, so a panel published complete has no holes); a
+            // block the diagonal cuts is loaded with a mask
+            const int ca = tmask_class(p.tmask_a, i * BM, BM, kb * BK, BK);
+            const int cb = tmask_class(p.tmask_b, j * BN, BN, kb * BK, BK);
+            const bool idle = (ca == 2 || cb == 2);
+            if (ca == 2 || (idle && da != DEC_PRODUCE)) da = DEC_SKIP;
+            if (cb == 2 || (idle && db != DEC_PRODUCE)) db = DEC_SKIP;
+            sm.part[q % DEC] = (ca == 1 ? 1 : 0) | (cb == 1 ? 2 : 0) | (idle ? 4 : 0);
+        } else {
+            (void)kb;
+        }
         sm.dec_a[q % DEC] = da;
         sm.dec_b[q % DEC] = db;
         return (da == DEC_PACKED && p.mode_a == MODE_FIP && !sm.full_a) ||
@@ -493,28 +499,45 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         const int stage = q % STAGES;
         const int kleft = p.k - kb * BK;
         const uint32_t sa = smem_addr(sm.a[stage]), sb = smem_addr(sm.b[stage]);
-        const int part = sm.part[q % DEC];
-        if (sm.dec_a[q % DEC] == DEC_SKIP) {
-            la.skip();
-        } else if (sm.dec_a[q % DEC] == DEC_PACKED) {
-            load_packed_tile<T, BM, BK, THREADS>(
-                sa, p.pack_a + ((int64_t)i * p.kt + kb) * (BM * BK), tid);
-            la.skip();
-        } else if (part & 1) {
-            la.issue_masked(sa, kleft, kb * BK, p.tmask_a, tid);
+        if constexpr (TMASK) {
+            const int part = sm.part[q % DEC];
+            if (sm.dec_a[q % DEC] == DEC_SKIP) {
+                la.skip();
+            } else if (sm.dec_a[q % DEC] == DEC_PACKED) {
+                load_packed_tile<T, BM, BK, THREADS>(
+                    sa, p.pack_a + ((int64_t)i * p.kt + kb) * (BM * BK), tid);
+                la.skip();
+            } else if (part & 1) {
+                la.issue_masked(sa, kleft, kb * BK, p.tmask_a, tid);
+            } else {
+                la.issue(sa, kleft, tid);
+            }
+            if (sm.dec_b[q % DEC] == DEC_SKIP) {
+                lb.skip();
+            } else if (sm.dec_b[q % DEC] == DEC_PACKED) {
+                load_packed_tile<T, BN, BK, THREADS>(
+                    sb, p.pack_b + ((int64_t)j * p.kt + kb) * (BN * BK), tid);
+                lb.skip();
+            } else if (part & 2) {
+                lb.issue_masked(sb, kleft, kb * BK, p.tmask_b, tid);
+            } else {
+                lb.issue(sb, kleft, tid);
+            }
         } else {
-            la.issue(sa, kleft, tid);
-        }
-        if (sm.dec_b[q % DEC] == DEC_SKIP) {
-            lb.skip();
-        } else if (sm.dec_b[q % DEC] == DEC_PACKED) {
-            load_packed_tile<T, BN, BK, THREADS>(
-                sb, p.pack_b + ((int64_t)j * p.kt + kb) * (BN * BK), tid);
-            lb.skip();
-        } else if (part & 2) {
-            lb.issue_masked(sb, kleft, kb * BK, p.tmask_b, tid);
-        } else {
-            lb.issue(sb, kleft, tid);
+            if (sm.dec_a[q % DEC] == DEC_PACKED) {
+                load_packed_tile<T, BM, BK, THREADS>(
+                    sa, p.pack_a + ((int64_t)i * p.kt + kb) * (BM * BK), tid);
+                la.skip();
+            } else {
+                la.issue(sa, kleft, tid);
+            }
+            if (sm.dec_b[q % DEC] == DEC_PACKED) {
+                load_packed_tile<T, BN, BK, THREADS>(
+                    sb, p.pack_b + ((int64_t)j * p.kt + kb) * (BN * BK), tid);
+                lb.skip();
+            } else {
+                lb.issue(sb, kleft, tid);
+            }
         }
     }
 
@@ -608,9 +631,11 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
 
     // Accumulates op(A)[tile rows, kb0*BK : kb1*BK] * op(B)[..., tile cols] into acc, packing
     // operand tiles on the way where this tile is a producer.
-    // HALF_ROWS: also compile the half-height micro-tile for tiles whose lower row chunks lie
-    // past m (worth its extra code only where most tiles are fringe tiles: grouped problems).
-    template <bool HALF_ROWS = false>
+    // FRINGE: compile fringe-tile shortcuts; 1: the last k-block trimmed to its rows of k and
+    // idle warps skipping the FMA loop, 2: also the half-height micro-tile for tiles whose
+    // lower row chunks lie past m.  They pay where most tiles are fringe tiles (grouped
+    // problems); elsewhere their registers cost the full tiles more than they save.
+    template <int FRINGE = 0>
     static __device__ void run_segment(const GemmParams<T> &p, Smem &sm, int i, int j,
                                        int kb0, int kb1, T (&acc)[TM][TN], unsigned int epoch)
     {
@@ -619,8 +644,8 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
         const int nkb = kb1 - kb0;
         // fringe tiles: a warp whose columns all lie past n has nothing to compute; if every
         // row chunk but the first lies past m, only the first is computed
-        const bool warp_idle = j * BN + ((tid & ~31) / TX) * CH >= p.n;
-        const bool half_rows = i * BM + BM / NCM >= p.m;
+        const bool warp_idle = FRINGE >= 1 && j * BN + ((tid & ~31) / TX) * CH >= p.n;
+        const bool half_rows = FRINGE >= 2 && i * BM + BM / NCM >= p.m;
 
 #pragma unroll
         for (int ii = 0; ii < TM; ++ii)
@@ -684,11 +709,12 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
             const bool ahead = (tid == 0) && (it + STAGES < nkb);
             Words w{0ull, 0ull};
             if (ahead) w = fetch_words(p, sm, i, j, kb0 + it + STAGES);
-            if (!warp_idle && !(sm.part[it % DEC] & 4)) {
+            if (!warp_idle && !(TMASK && (sm.part[it % DEC] & 4))) {
                 // the tile's last k-block computes only its rows of k that exist
                 const int kin = p.k - (kb0 + it) * BK;
-                const int kext = kin >= BK ? BK : ((kin + UNROLL - 1) / UNROLL) * UNROLL;
-                if (HALF_ROWS && half_rows)
+                const int kext =
+                    (FRINGE == 0 || kin >= BK) ? BK : ((kin + UNROLL - 1) / UNROLL) * UNROLL;
+                if (FRINGE >= 2 && half_rows)
                     compute<1>(sm.a[stage], sm.b[stage], acc, tx, ty, kext);
                 else
                     compute<NCM>(sm.a[stage], sm.b[stage], acc, tx, ty, kext);
@@ -868,7 +894,7 @@ template <typename T, bool ACONTIG, bool BCONTIG, typename C = TileCfg<T>> struc
 // fresh epoch too.  (The next launch on the stream starts only after this one has finished,
 // and every CTA has read the counter before it counts itself finished.)  The counter is held
 // in a register: only thread 0 uses it, so its load latency hides behind the first loads.
-template <typename T, bool ACONTIG, bool BCONTIG>
+template <typename T, bool ACONTIG, bool BCONTIG, bool TMASK = false>
 __global__ void __launch_bounds__(TileCfg<T>::THREADS, TileCfg<T>::MIN_BLOCKS)
     gemm_kernel(const GemmParams<T> p)
 {
@@ -876,7 +902,7 @@ __global__ void __launch_bounds__(TileCfg<T>::THREADS, TileCfg<T>::MIN_BLOCKS)
     GemmSmem<T> &sm = *reinterpret_cast<GemmSmem<T> *>(smem_raw);
     unsigned int epoch = 0u;
     if (threadIdx.x == 0) epoch = *(volatile unsigned int *)p.launch_count + 1u;
-    Kernel<T, ACONTIG, BCONTIG>::run(p, sm, epoch);
+    Kernel<T, ACONTIG, BCONTIG, TileCfg<T>, TMASK>::run(p, sm, epoch);
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(p.done_count, 1u) == gridDim.x - 1) {
@@ -946,33 +972,41 @@ template <typename T> inline size_t gemm_smem_bytes()
     return sizeof(GemmSmem<T>);
 }
 
-template <typename T, bool AC, bool BC> cudaError_t configure_gemm()
+template <typename T, bool AC, bool BC, bool TM = false> cudaError_t configure_gemm()
 {
     static bool configured = false;
     if (configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<T, AC, BC>,
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<T, AC, BC, TM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(gemm_smem_bytes<T>()));
     if (e == cudaSuccess) configured = true;
     return e;
 }
 
-template <typename T, bool AC, bool BC>
+template <typename T, bool AC, bool BC, bool TM>
 cudaError_t launch_gemm_t(const GemmParams<T> &p, cudaStream_t s)
 {
-    cudaError_t e = configure_gemm<T, AC, BC>();
+    cudaError_t e = configure_gemm<T, AC, BC, TM>();
     if (e != cudaSuccess) return e;
-    gemm_kernel<T, AC, BC><<<p.grid, TileCfg<T>::THREADS, gemm_smem_bytes<T>(), s>>>(p);
+    gemm_kernel<T, AC, BC, TM><<<p.grid, TileCfg<T>::THREADS, gemm_smem_bytes<T>(), s>>>(p);
     return cudaGetLastError();
+}
+
+// Triangular-operand launches (TRMM) take the instantiation that handles masks.
+template <typename T, bool AC, bool BC>
+cudaError_t launch_gemm_mask(const GemmParams<T> &p, cudaStream_t s)
+{
+    return (p.tmask_a || p.tmask_b) ? launch_gemm_t<T, AC, BC, true>(p, s)
+                                    : launch_gemm_t<T, AC, BC, false>(p, s);
 }
 
 template <typename T> cudaError_t launch_gemm_impl(const GemmParams<T> &p, cudaStream_t s)
 {
     if (p.a_contig_m)
-        return p.b_contig_n ? launch_gemm_t<T, true, true>(p, s)
-                            : launch_gemm_t<T, true, false>(p, s);
-    return p.b_contig_n ? launch_gemm_t<T, false, true>(p, s)
-                        : launch_gemm_t<T, false, false>(p, s);
+        return p.b_contig_n ? launch_gemm_mask<T, true, true>(p, s)
+                            : launch_gemm_mask<T, true, false>(p, s);
+    return p.b_contig_n ? launch_gemm_mask<T, false, true>(p, s)
+                        : launch_gemm_mask<T, false, false>(p, s);
 }
 
 template <typename T, bool AC, bool BC> int blocks_per_sm_one()
@@ -1031,6 +1065,21 @@ cudaError_t launch_scale_impl(T *C, int64_t ldc, int m, int n, T beta, int tri, 
 }
 
 }  // namespace gfip
+
+// The triangular-operand (TRMM) instantiations of the GEMM kernel are compiled in a
+// translation unit of their own (gfip_f64_tmask.cu, gfip_f32_tmask.cu), so the two halves
+// build in parallel.
+#define GFIP_TMASK_LAUNCHERS(PREFIX, T)                                                        \
+    namespace gfip {                                                                          \
+    PREFIX template cudaError_t launch_gemm_t<T, true, true, true>(const GemmParams<T> &,      \
+                                                                   cudaStream_t);              \
+    PREFIX template cudaError_t launch_gemm_t<T, true, false, true>(const GemmParams<T> &,     \
+                                                                    cudaStream_t);             \
+    PREFIX template cudaError_t launch_gemm_t<T, false, true, true>(const GemmParams<T> &,     \
+                                                                    cudaStream_t);             \
+    PREFIX template cudaError_t launch_gemm_t<T, false, false, true>(const GemmParams<T> &,    \
+                                                                     cudaStream_t);            \
+    }
 
 // Explicit instantiation of the launchers for one element type.
 #define GFIP_INSTANTIATE(T)                                                                   \
