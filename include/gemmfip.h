@@ -28,7 +28,11 @@
  *     (transa=1, transb=2, m=3, n=4, k=5, alpha=6, A=7, lda=8, B=9, ldb=10, beta=11, C=12,
  *      ldc=13),
  * exactly as xerbla would report it; positive values are the GFIP_ERR_* runtime errors.
- * On any nonzero return nothing has been launched and C is unchanged.
+ * A negative return, or a GFIP_ERR_HANDLE / GFIP_ERR_WORKSPACE / GFIP_ERR_NULLPTR /
+ * GFIP_ERR_SIZE / GFIP_ERR_ARG return, happens before anything is launched: C (B for
+ * TRMM and TRSM) is unchanged.  GFIP_ERR_CUDA means a launch or copy failed; a call that
+ * enqueues several kernels (pack-then-compute, TRMM, TRSM) may then have enqueued the
+ * earlier ones, and the output operand is undefined.
  *
  * Quick returns (reference-BLAS rules): m == 0 or n == 0, or (alpha == 0 or k == 0) and
  * beta == 1, return 0 with nothing launched; alpha == 0 or k == 0 scales C by beta

@@ -575,6 +575,14 @@ int trsm_entry(gfip_handle_t handle, char side, char uplo, char transa, char dia
     if (m == 0 || n == 0) return GFIP_OK;
     if (too_big(m) || too_big(n) || too_big(lda) || too_big(ldb)) return GFIP_ERR_SIZE;
     if (B == nullptr) return GFIP_ERR_NULLPTR;
+    if (alpha != T(0)) {
+        // every check before the first launch: the largest update's workspace (all of B
+        // against one block) bounds every later one
+        if (A == nullptr) return GFIP_ERR_NULLPTR;
+        if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
+        const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)m, (int)n, gfip::TRSM_NB);
+        if (total_bytes(h, pl) > h->ws_bytes) return GFIP_ERR_WORKSPACE;
+    }
     if (alpha != T(1)) {   // B := alpha B (alpha == 0: zeros, B not read)
         if (gfip::launch_scale<T>(B, ldb, (int)m, (int)n, alpha, gfip::TRI_NONE, h->stream) !=
             cudaSuccess)

@@ -173,3 +173,22 @@ def test_large_sampled_residual(runner, dtype, side, uplo, ta, diag, m, n):
     assert np.isfinite(inputs.as_matrix(X, m, n, m + 7)).all()
     ii, jj = inputs.sample_indices(rng, m, n, 4096, full_rows=2, full_cols=2)
     residual_check(side, uplo, ta, diag, m, n, 1.5, A, na + 7, B0, m + 7, X, ii, jj)
+
+
+@pytest.mark.parametrize("solver", ["trsm", "trmm"])
+def test_small_workspace_changes_nothing(runner, solver):
+    """A workspace too small for the call is reported before anything is launched: B keeps
+    its bytes (TRSM scales B by alpha first, so the check must come before that)."""
+    rng = np.random.Generator(np.random.PCG64(24))
+    m, n = 300, 200
+    A = system(rng, m, m, "L", "N", np.float64)
+    B0 = inputs.colmajor(rng, m, n, m + 3)
+    dA = torch.from_numpy(A).to(runner.dev)
+    dB = torch.from_numpy(B0.copy()).to(runner.dev)
+    h = g.Handle(workspace_bytes=1 << 16)
+    h.bind_stream()
+    fn = g.gfip_trsm if solver == "trsm" else g.gfip_trmm
+    rc = fn(8, h.h, "L", "L", "N", "N", m, n, 2.0, dA.data_ptr(), m, dB.data_ptr(), m + 3)
+    assert rc == g.GFIP_ERR_WORKSPACE
+    torch.cuda.synchronize()
+    assert np.array_equal(dB.cpu().numpy().view(np.uint8), B0.view(np.uint8))
