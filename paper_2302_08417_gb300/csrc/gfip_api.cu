@@ -118,7 +118,8 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI
     pl.tiles = tri ? pl.mt * (pl.mt + 1) / 2 : pl.mt * pl.nt;
 
     // Schedule: data-parallel waves of whole tiles, then the remaining tiles (the partial
-    // wave plus one full wave) split evenly along k over all CTAs.
+    // wave, with one full wave more when the partial one is short) split evenly along k over
+    // all CTAs.
     const int bps = std::max(1, blocks_per_sm<T>(h));
     const int full = h->sms * bps;
     const int64_t total_iters = (int64_t)pl.tiles * pl.kt;

@@ -25,8 +25,8 @@ enum OperandMode : int {
 };
 
 // Tile shape of one element type.  The CTA computes a BM x BN tile of C, stepping through
-// k in blocks of BK; each thread owns a (2*CH) x (2*CH) register micro-tile (CH = elements
-// per 16 bytes).
+// k in blocks of BK; each thread owns an (NCM*CH) x (NCN*CH) register micro-tile (CH =
+// elements per 16 bytes).
 template <typename T> struct TileCfg;
 
 // FP64: the DFMA pipe (2 lanes per clock per SM) is the bound at every size, so small tiles

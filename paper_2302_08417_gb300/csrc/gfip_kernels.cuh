@@ -16,12 +16,13 @@
 //    k-block by k-block, computes with it, and in the same pass writes the staged tile image
 //    to the packed buffer and publishes it (an epoch-tagged ready word, release order).  Every
 //    other tile looks the ready word up (acquire load) a few k-blocks ahead: published tiles
-//    are read packed, the rest raw.  Nothing ever waits for another CTA (Sec. 3.5: packers
-//    pack their own share; only consumers that come later use the packed data).
+//    are read packed, the rest raw.  Nothing ever waits for another CTA (the multithreaded
+//    scheme of Sec. 3.5 synchronises once after a collaborative pack; here only tiles that
+//    run after a producer use what it packed).
 //
 //  * One code path for all sizes.  Tiles run as data-parallel waves over the persistent
-//    CTAs; the tiles of the last, partial wave (plus one full wave) are split evenly along k
-//    over all CTAs ("stream-K"), and split tiles are summed in a fixed order by whichever CTA
+//    CTAs; the tiles of the last, partial wave (with one full wave more when the partial one
+//    would give each CTA a short run) are split evenly along k over all CTAs ("stream-K"), and split tiles are summed in a fixed order by whichever CTA
 //    finishes last.  The split points depend only on the problem shape and the grid, so every
 //    variant (fused, direct, pack-then-compute) and every pack policy produces identical
 //    bits: packing changes where a tile is read from, never its value.
