@@ -398,6 +398,74 @@ def _span_to_device(X):
     return torch.as_strided(flat, (rows, cols), (1, ld))
 
 
+# Column blocks of C in the pipelined host path: none below this many columns of C.
+HOST_BLOCK_COLS = 1024
+
+
+def _gemm_host(A, B, C_h, alpha, beta, transa, transb, variant, handle):
+    """The end-to-end path: host operands in, host result out.  Each operand's storage span
+    (ld*(cols-1) + rows elements) is copied as is, so leading dimensions are kept.
+
+    With op(B) = B ('N') and at least two blocks of HOST_BLOCK_COLS columns, the product runs
+    as a pipeline over column blocks of C: A goes up first, then block q's columns of B (and
+    of C unless beta == 0 and ldc == m) go up on a copy stream while block q-1 computes, and
+    block q's result comes down on another stream while block q+1 computes; every block is
+    one call of the library on the device.  (Results equal the single device call's within
+    the bound; the blocks' schedules differ, so not necessarily bit for bit.)  Otherwise:
+    copy all, one call, copy back."""
+    import torch
+    n = C_h.shape[1]
+    blocks = n // HOST_BLOCK_COLS if transb.upper() == "N" else 1
+    if blocks < 2 or C_h.shape[0] == 0 or B.shape[0] == 0:
+        dA, dB, dC = (_span_to_device(X) for X in (A, B, C_h))
+        gemm(dA, dB, dC, alpha, beta, transa, transb, variant, handle)
+        _span(C_h).copy_(_span(dC), non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return C_h
+    dev = torch.device("cuda", torch.cuda.current_device())
+    compute = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    s_in.wait_stream(compute)     # device buffers below are allocated on `compute`
+    spanB, spanC = _span(B), _span(C_h)
+    dB_flat = torch.empty(spanB.numel(), dtype=B.dtype, device=dev)
+    dC_flat = torch.empty(spanC.numel(), dtype=C_h.dtype, device=dev)
+    ldb, ldc = _colmajor_ld(B, "B"), _colmajor_ld(C_h, "C")
+    k, m = B.shape[0], C_h.shape[0]
+    bounds = [n * q // blocks for q in range(blocks + 1)]
+    # C goes up when beta reads it, or when its rows m..ldc-1 lie inside a block's span
+    # (they travel up and back down unchanged)
+    upload_c = beta != 0.0 or ldc > m
+    with torch.cuda.stream(s_in):
+        dA = _span_to_device(A)
+        ins = []
+        for q in range(blocks):
+            j0, j1 = bounds[q], bounds[q + 1]
+            b0, b1 = j0 * ldb, (j1 - 1) * ldb + k
+            dB_flat[b0:b1].copy_(spanB[b0:b1], non_blocking=True)
+            if upload_c:
+                c0, c1 = j0 * ldc, (j1 - 1) * ldc + m
+                dC_flat[c0:c1].copy_(spanC[c0:c1], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s_in)
+            ins.append(ev)
+    for q in range(blocks):
+        j0, j1 = bounds[q], bounds[q + 1]
+        compute.wait_event(ins[q])
+        dBq = torch.as_strided(dB_flat, (k, j1 - j0), (1, ldb), j0 * ldb)
+        dCq = torch.as_strided(dC_flat, (m, j1 - j0), (1, ldc), j0 * ldc)
+        gemm(dA, dBq, dCq, alpha, beta, transa, "N", variant, handle)
+        done = torch.cuda.Event()
+        done.record(compute)
+        s_out.wait_event(done)
+        with torch.cuda.stream(s_out):
+            c0, c1 = j0 * ldc, (j1 - 1) * ldc + m
+            spanC[c0:c1].copy_(dC_flat[c0:c1], non_blocking=True)
+    # the last download waits on the last block, which waits on every upload: once it is
+    # done, no stream still uses the device buffers
+    s_out.synchronize()
+    return C_h
+
+
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, transa: str = "N",
          transb: str = "N", variant: str = "fused", handle: Handle | None = None):
     """``C := alpha*op(A)*op(B) + beta*C`` on column-major 2-D tensors (float64 or float32).
@@ -410,18 +478,12 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, transa: str = "N",
     import torch
     host = not A.is_cuda
     if host:
-        # end-to-end path: host operands in, host result out; each operand's storage span
-        # (ld*(cols-1) + rows elements) is copied as is, so leading dimensions are kept
         C_h = C
         if C_h is None:
             m_ = A.shape[0] if transa.upper() == "N" else A.shape[1]
             n_ = B.shape[1] if transb.upper() == "N" else B.shape[0]
             C_h = torch.empty((n_, m_), dtype=A.dtype, pin_memory=True).t()
-        dA, dB, dC = (_span_to_device(X) for X in (A, B, C_h))
-        gemm(dA, dB, dC, alpha, beta, transa, transb, variant, handle)
-        _span(C_h).copy_(_span(dC), non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return C_h
+        return _gemm_host(A, B, C_h, alpha, beta, transa, transb, variant, handle)
     dtype = A.dtype
     if dtype not in (torch.float64, torch.float32) or B.dtype != dtype:
         raise TypeError("A and B must both be float64 or both float32")
