@@ -72,11 +72,22 @@ typedef struct gfip_handle_s *gfip_handle_t;
 
 /* Pack policies for gfip_set_pack_policy(). */
 #define GFIP_PACK_AUTO 0        /* Sec. 3.3 option table: pack A iff > 1 tile column, B iff > 1 tile
-                                   row, and only when some tiles run after the first wave of CTAs  */
+                                   row; with line producers (GFIP_PACKER_LINE) only when some
+                                   tiles run after the first wave of CTAs                           */
 #define GFIP_PACK_NONE 1        /* never pack (the fused kernel then equals the direct variant)          */
 #define GFIP_PACK_A 2           /* pack A panels only                                                   */
 #define GFIP_PACK_B 3           /* pack B panels only                                                   */
 #define GFIP_PACK_BOTH 4        /* pack both operands regardless of reuse                               */
+
+/* Packers for gfip_set_packer(): which CTAs write the packed copies in the fused routines. */
+#define GFIP_PACKER_AUTO 0      /* SHARED for FP32 GEMMs with at least 16 k-blocks of work per
+                                   CTA (tiles x k-blocks >= 16 x CTAs), else LINE                */
+#define GFIP_PACKER_LINE 1      /* the first tile column packs A, the first tile row B, while
+                                   computing their own tiles (Alg. 1, Sec. 3.2)                   */
+#define GFIP_PACKER_SHARED 2    /* every CTA first packs an equal share of all packed tiles,
+                                   k-block by k-block over the panels, then runs its tiles
+                                   (the collaborative packing of Sec. 3.5).  Only for dense
+                                   operands and a full C: SYRK and TRMM always use LINE      */
 
 /* Creates a handle bound to the CURRENT CUDA device; its stream is the legacy default
  * stream until gfip_set_stream().  Returns GFIP_ERR_DEVICE if that device is not sm_103,
@@ -107,6 +118,10 @@ int gfip_set_workspace(gfip_handle_t handle, void *dev_ptr, size_t bytes);
 /* Chooses which operands the fused routines pack (GFIP_PACK_*); testing and tuning aid.
  * The result bits do not depend on the policy. */
 int gfip_set_pack_policy(gfip_handle_t handle, int policy);
+
+/* Chooses who packs in the fused routines (GFIP_PACKER_*); testing and tuning aid.
+ * GFIP_ERR_ARG for an unknown value.  The result bits do not depend on the packer. */
+int gfip_set_packer(gfip_handle_t handle, int packer);
 
 /* Fused-in-packing GEMM (the method of Sec. 3.2), FP64 and FP32. */
 int gfip_dgemm(gfip_handle_t handle, char transa, char transb, int64_t m, int64_t n, int64_t k,

@@ -22,8 +22,10 @@ constexpr size_t kAlign = 256;
 constexpr size_t kHeader = 256;             // status word, launch counters, spare
 constexpr size_t kLaunchCountOffset = 64;   // header word: GEMM launches so far (epochs)
 constexpr size_t kDoneCountOffset = 128;    // header word: finished CTAs of the running launch
+constexpr size_t kPackCountOffset = 192;    // header word: tiles packed by shared packing
 constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
 constexpr int kMinSplitRun = 8;              // shortest k run per CTA in a split wave
+constexpr int kSharedMinRun = 16;            // AUTO packer: shared from this many k-blocks per CTA
 constexpr unsigned long long kOzakiWaitNs = 2000000000ull;  // 2 s per pipeline wait
 
 struct Handle {
@@ -37,6 +39,7 @@ struct Handle {
     // kernel of this handle tagged with an older epoch).  Data never lives below this mark.
     size_t ctrl_bytes = 0;
     int pack_policy = GFIP_PACK_AUTO;
+    int packer = GFIP_PACKER_AUTO;
     unsigned long long oz_wait_ns = kOzakiWaitNs;  // budget of the emulation kernel's waits
     int oz_inject = 0;                             // test hook (gfip_debug_ozaki_timeout)
     int last_launches = 0;
@@ -92,6 +95,7 @@ template <typename T> struct Plan {
     int grid = 0, dp_tiles = 0;
     int64_t sk_iters = 0;
     int mode_a = gfip::MODE_RAW, mode_b = gfip::MODE_RAW;
+    bool shared = false;        // all CTAs pack first (else the first tile line packs)
     // workspace layout (byte offsets from the workspace base)
     size_t ctrl_needed = 0;
     size_t off_count = 0, off_state_a = 0, off_state_b = 0;
@@ -105,8 +109,21 @@ template <typename T> int blocks_per_sm(Handle *h)
     return slot;
 }
 
+// Who packs when the packer is AUTO: all CTAs up front (shared) for FP32 GEMMs that give each
+// CTA at least kSharedMinRun k-blocks of work, where the FFMA loop pays for every
+// element-wise raw load a tile makes and the short pre-pass before the tiles costs less
+// (measured: +1.2 % to +4.3 % over line producers from 1536^3 to 8192^3, -1 % to -5 % at
+// 768^3 and 1024^3 with 3 and 7 k-blocks per CTA); the first tile line (Alg. 1) for FP64,
+// whose DFMA-bound loop hides the raw loads (both packers measured equal at 8192^3), and
+// for short runs, where the pre-pass would not be repaid.
+template <typename T> bool auto_shared(const Plan<T> &pl)
+{
+    return sizeof(T) == 4 && (int64_t)pl.tiles * pl.kt >= (int64_t)kSharedMinRun * pl.grid;
+}
+
 template <typename T>
-Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI_NONE)
+Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI_NONE,
+                  bool masked = false)
 {
     using Cfg = gfip::TileCfg<T>;
     Plan<T> pl;
@@ -143,6 +160,12 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI
         pl.sk_iters = (int64_t)sk_tiles * pl.kt;
     }
 
+    // Who packs: shared packing only for whole rectangles of dense operands (a triangle's
+    // panels are shared by both roles, and masked blocks are never packed whole).
+    if (v == Variant::Fused && tri == gfip::TRI_NONE && !masked)
+        pl.shared = h->packer == GFIP_PACKER_SHARED ||
+                    (h->packer == GFIP_PACKER_AUTO && auto_shared<T>(pl));
+
     // Which operands are packed, and how (Sec. 3.3 option table for the fused variant).
     switch (v) {
     case Variant::Direct:
@@ -169,11 +192,12 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI
             break;
         default: {
             // AUTO: Sec. 3.3's table (an A panel is reused only across tile columns, a B
-            // panel only across tile rows), read for a GPU: a packed copy pays off only for
-            // tiles that run after its producer, i.e. when a whole data-parallel wave (which
-            // holds the producers) runs before other tiles; tiles running side by side with
-            // the producer read the raw operand
-            const bool later = pl.tiles > pl.grid && pl.dp_tiles >= pl.grid;
+            // panel only across tile rows), read for a GPU.  With line producers a packed
+            // copy pays off only for tiles that run after its producer, i.e. when a whole
+            // data-parallel wave (which holds the producers) runs before other tiles; tiles
+            // running side by side with the producer read the raw operand.  Shared packing
+            // publishes every panel before the tiles start, so reuse alone decides.
+            const bool later = pl.shared || (pl.tiles > pl.grid && pl.dp_tiles >= pl.grid);
             pl.mode_a = (pl.nt > 1 && later) ? gfip::MODE_FIP : gfip::MODE_RAW;
             pl.mode_b = (pl.mt > 1 && later) ? gfip::MODE_FIP : gfip::MODE_RAW;
             break;
@@ -181,6 +205,10 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI
         }
         break;
     }
+    // (the count of packed tiles keeps twice their number in 32 bits)
+    const int64_t units = (int64_t)((pl.mode_a == gfip::MODE_FIP ? pl.mt : 0) +
+                                    (pl.mode_b == gfip::MODE_FIP ? pl.nt : 0)) * pl.kt;
+    if (units == 0 || units >= (int64_t(1) << 30)) pl.shared = false;
     if (tri) {
         // SYRK: both operand roles read panels of the same matrix A, so one packed copy
         // serves both; any packing policy packs A's panels once (or not at all)
@@ -264,7 +292,7 @@ int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t
                 int64_t k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb, T beta,
                 T *C, int64_t ldc, int tmask_a, int tmask_b)
 {
-    Plan<T> pl = make_plan<T>(h, v, (int)m, (int)n, (int)k, tri);
+    Plan<T> pl = make_plan<T>(h, v, (int)m, (int)n, (int)k, tri, tmask_a || tmask_b);
     if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
     if (total_bytes(h, pl) > h->ws_bytes) return GFIP_ERR_WORKSPACE;
 
@@ -308,8 +336,12 @@ int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t
     p.tri = tri;
     // the operand whose first tile line packs: A (first tile column) unless the triangle is
     // the upper one, whose first tile line is the first tile row (B's producers)
-    p.a_produces = (tri != gfip::TRI_UPPER) ? 1 : 0;
-    p.b_produces = (tri == gfip::TRI_NONE || tri == gfip::TRI_UPPER) ? 1 : 0;
+    p.a_produces = (tri != gfip::TRI_UPPER && !pl.shared) ? 1 : 0;
+    p.b_produces = ((tri == gfip::TRI_NONE || tri == gfip::TRI_UPPER) && !pl.shared) ? 1 : 0;
+    p.shared_pack = pl.shared ? 1 : 0;
+    p.pack_units = pl.shared ? (int64_t)((pl.mode_a == gfip::MODE_FIP ? pl.mt : 0) +
+                                         (pl.mode_b == gfip::MODE_FIP ? pl.nt : 0)) * pl.kt
+                             : 0;
     p.tmask_a = tmask_a;
     p.tmask_b = tmask_b;
     p.state_a = reinterpret_cast<unsigned long long *>(h->ws + pl.off_state_a);
@@ -321,6 +353,7 @@ int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t
     p.status = reinterpret_cast<unsigned int *>(h->ws);
     p.launch_count = reinterpret_cast<unsigned int *>(h->ws + kLaunchCountOffset);
     p.done_count = reinterpret_cast<unsigned int *>(h->ws + kDoneCountOffset);
+    p.pack_count = reinterpret_cast<unsigned long long *>(h->ws + kPackCountOffset);
 
     int launches = 0;
     if (v == Variant::PackThenCompute) {
@@ -493,7 +526,8 @@ template <typename T>
 size_t trmm_workspace_impl(Handle *h, char side, int64_t m, int64_t n)
 {
     const bool left = side == 'L' || side == 'l';
-    const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)m, (int)n, (int)(left ? m : n));
+    const Plan<T> pl =
+        make_plan<T>(h, Variant::Fused, (int)m, (int)n, (int)(left ? m : n), gfip::TRI_NONE, true);
     return round_up(total_bytes(h, pl), kAlign) + round_up((size_t)m * n * sizeof(T), kAlign);
 }
 
@@ -526,7 +560,8 @@ int trmm_entry(gfip_handle_t handle, char side, char uplo, char transa, char dia
     const bool left = side == 'L' || side == 'l';
     const bool unit = diag == 'U' || diag == 'u';
     const int64_t kdim = left ? m : n;
-    const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)m, (int)n, (int)kdim);
+    const Plan<T> pl =
+        make_plan<T>(h, Variant::Fused, (int)m, (int)n, (int)kdim, gfip::TRI_NONE, true);
     const size_t w_off = round_up(total_bytes(h, pl), kAlign);
     const size_t w_bytes = (size_t)m * n * sizeof(T);
     if (w_off + w_bytes > h->ws_bytes) return GFIP_ERR_WORKSPACE;
@@ -724,6 +759,15 @@ int gfip_set_pack_policy(gfip_handle_t handle, int policy)
     if (h == nullptr) return GFIP_ERR_HANDLE;
     if (policy < GFIP_PACK_AUTO || policy > GFIP_PACK_BOTH) return GFIP_ERR_ARG;
     h->pack_policy = policy;
+    return GFIP_OK;
+}
+
+int gfip_set_packer(gfip_handle_t handle, int packer)
+{
+    Handle *h = get(handle);
+    if (h == nullptr) return GFIP_ERR_HANDLE;
+    if (packer < GFIP_PACKER_AUTO || packer > GFIP_PACKER_SHARED) return GFIP_ERR_ARG;
+    h->packer = packer;
     return GFIP_OK;
 }
 

@@ -98,6 +98,8 @@ template <typename T> struct GemmParams {
     int tri;          // TRI_NONE: all of C; TRI_LOWER / TRI_UPPER: that triangle (SYRK)
     int a_produces;   // the first tile column packs the A panels
     int b_produces;   // the first tile row packs the B panels
+    int shared_pack;  // all CTAs pack the packed operands' tiles first (no line producers)
+    int64_t pack_units;  // shared packing: (panel, k-block) tiles to pack in all
     int tmask_a;      // triangular mask of op(A) (TRMM), 0 = dense; see TriMask
     int tmask_b;      // triangular mask of op(B)
     int grid;         // persistent CTAs
@@ -114,6 +116,7 @@ template <typename T> struct GemmParams {
     unsigned int *status;            // device status bits (GFIP_STATUS_*)
     unsigned int *launch_count;      // launches so far (the epoch of a launch is this + 1)
     unsigned int *done_count;        // CTAs of the current launch that have finished
+    unsigned long long *pack_count;  // shared packing: epoch-tagged count of packed tiles
 };
 
 // Parameters of the pack kernel of the pack-then-compute variant.

@@ -370,6 +370,7 @@ template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     int dec_b[2 * Cfg::STAGES];
     int part[2 * Cfg::STAGES];   // bit 0 (1): the A (B) block is cut by a triangular mask
     int full_a, full_b;  // the tile's whole A (B) panel is already published
+    int watch;           // shared packing: the count of packed tiles is not complete yet
     int flag;
 };
 
@@ -619,6 +620,16 @@ struct Kernel {
         }
     }
 
+    // Value of the count of packed tiles once shared packing is complete in this launch: the
+    // epoch in the upper half, twice the tiles in the lower (each tile counts 2, so a count
+    // is even and never equals a ready word, which is odd).
+    static __device__ __forceinline__ unsigned long long all_packed(const GemmParams<T> &p,
+                                                                    unsigned int epoch)
+    {
+        return (static_cast<unsigned long long>(epoch) << 32) |
+               (2ull * static_cast<unsigned long long>(p.pack_units));
+    }
+
     // Publishes the tiles this CTA produced at local k-block it (thread 0 only).
     static __device__ __forceinline__ void publish_produced(const GemmParams<T> &p,
                                                             const Smem &sm, int i, int j,
@@ -669,11 +680,18 @@ struct Kernel {
         lb.init(p.B, p.ldb, j * BN, kb0 * BK, p.n, tid);
 
         if (tid == 0) {
-            // a panel whose producer finished it whole needs no per-k-block look-ups
+            // a panel whose producer finished it whole needs no per-k-block look-ups; with
+            // shared packing, every panel is whole once all CTAs have counted their tiles
+            // (until then thread 0 watches the count, loaded in place of the words)
+            const bool all = !TMASK && p.shared_pack &&
+                             ld_relaxed(p.pack_count) == all_packed(p, epoch);
+            sm.watch = !TMASK && p.shared_pack && !all;
             const bool fa = need_word(p.mode_a, prod_a(p, j), 0) &&
-                            ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) == ready_value(epoch);
+                            (all || ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) ==
+                                        ready_value(epoch));
             const bool fb = need_word(p.mode_b, prod_b(p, i), 0) &&
-                            ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) == ready_value(epoch);
+                            (all || ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) ==
+                                        ready_value(epoch));
             sm.full_a = fa;
             sm.full_b = fb;
             Words w[STAGES];
@@ -710,6 +728,10 @@ struct Kernel {
             const bool ahead = (tid == 0) && (it + STAGES < nkb);
             Words w{0ull, 0ull};
             if (ahead) w = fetch_words(p, sm, i, j, kb0 + it + STAGES);
+            // shared packing publishes no per-k-block words (they read as not ready); while
+            // the count of packed tiles is incomplete it travels in A's word slot (counts are
+            // even, ready words odd, so classify() never takes it for a ready word)
+            if (!TMASK && ahead && p.shared_pack && sm.watch) w.a = ld_relaxed(p.pack_count);
             if (!warp_idle && !(TMASK && (sm.part[it % DEC] & 4))) {
                 // the tile's last k-block computes only its rows of k that exist
                 const int kin = p.k - (kb0 + it) * BK;
@@ -721,6 +743,14 @@ struct Kernel {
                     compute<NCM>(sm.a[stage], sm.b[stage], acc, tx, ty, kext);
             }
             if (tid == 0) {
+                if (!TMASK && ahead && p.shared_pack && sm.watch &&
+                    w.a == all_packed(p, epoch)) {
+                    // every panel is packed: k-blocks from it + STAGES on read the copies
+                    sm.full_a = need_word(p.mode_a, false, 0);
+                    sm.full_b = need_word(p.mode_b, false, 0);
+                    sm.watch = 0;
+                    fence_acquire();
+                }
                 if (ahead && store_decisions(p, sm, i, j, kb0 + it + STAGES, w, it + STAGES, epoch))
                     fence_acquire();
                 // the pack stores of the previous k-block were ordered by this iteration's
@@ -849,12 +879,87 @@ struct Kernel {
         __syncthreads();
     }
 
+    // Shared packing (the collaborative packing of Sec. 3.5, read for a GPU): before its
+    // tiles, every CTA packs a share of the (panel, k-block) tiles of the packed operands.
+    // Unit u is k-block u / P of panel u % P (P = packed panels, A's first), CTA g takes u = g,
+    // g + grid, ...; the copies run 2 STAGES - 1 units ahead of the stores.  Completion is one
+    // epoch-tagged count of packed tiles, not a ready word per tile: a tile reads the raw
+    // operand until the count shows every CTA done, then the packed copies, after a single
+    // acquire fence (a fence per k-block stalls the warp of the thread that takes it).
+    static __device__ void share_pack(const GemmParams<T> &p, Smem &sm, unsigned int epoch)
+    {
+        // all 2 * STAGES stage buffers take pack units (A and B tiles have the same shape),
+        // so that up to 2 * STAGES - 1 units' copies are in flight
+        static_assert(BM == BN, "shared packing uses A and B stage buffers alike");
+        constexpr int NBUF = 2 * STAGES;
+        const int tid = threadIdx.x;
+        const int g = blockIdx.x;
+        const int pa = (p.mode_a == MODE_FIP) ? p.mt : 0;
+        const int pb = (p.mode_b == MODE_FIP) ? p.nt : 0;
+        const int64_t per_kb = pa + pb;
+        const int64_t units = per_kb * p.kt;
+        if (g >= units) return;
+        const int mine = static_cast<int>((units - 1 - g) / p.grid) + 1;
+        auto buf = [&](int r) -> T * { return (r % NBUF < STAGES) ? sm.a[r % NBUF]
+                                                                  : sm.b[r % NBUF - STAGES]; };
+        auto locate = [&](int r, int &panel, int &kb) {   // panel < pa: A panel, else B
+            const int64_t u = g + (int64_t)r * p.grid;
+            kb = static_cast<int>(u / per_kb);
+            panel = static_cast<int>(u % per_kb);
+        };
+        auto issue_unit = [&](int r) {
+            int x, kb;
+            locate(r, x, kb);
+            if (x < pa) {
+                LoadA l;
+                l.init(p.A, p.lda, x * BM, kb * BK, p.m, tid);
+                l.issue(smem_addr(buf(r)), p.k - kb * BK, tid);
+            } else {
+                LoadB l;
+                l.init(p.B, p.ldb, (x - pa) * BN, kb * BK, p.n, tid);
+                l.issue(smem_addr(buf(r)), p.k - kb * BK, tid);
+            }
+        };
+#pragma unroll
+        for (int q = 0; q < NBUF - 1; ++q) {
+            if (q < mine) issue_unit(q);
+            cp_async_commit();
+        }
+        for (int r = 0; r < mine; ++r) {
+            cp_async_wait<NBUF - 2>();
+            __syncthreads();
+            int x, kb;
+            locate(r, x, kb);
+            if (x < pa)
+                store_packed_tile<T, BM, BK, THREADS>(
+                    p.pack_a + ((int64_t)x * p.kt + kb) * (BM * BK), buf(r), tid);
+            else
+                store_packed_tile<T, BN, BK, THREADS>(
+                    p.pack_b + ((int64_t)(x - pa) * p.kt + kb) * (BN * BK), buf(r), tid);
+            // refills the buffer stored in the previous iteration (read before the barrier)
+            const int q = r + NBUF - 1;
+            if (q < mine) issue_unit(q);
+            cp_async_commit();
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+        if (tid == 0) {
+            // count this CTA's tiles once its stores (ordered by the barrier) are visible;
+            // the count reaching pack_units tells a tile that every panel is complete
+            __threadfence();
+            const unsigned long long tag = static_cast<unsigned long long>(epoch) << 32;
+            atomicMax(p.pack_count, tag);
+            atomicAdd(p.pack_count, 2ull * static_cast<unsigned long long>(mine));
+        }
+    }
+
     // Thread 0's `epoch` tags the ready words and arrival counters this launch writes (only
     // thread 0 of a CTA reads or writes them).
     static __device__ void run(const GemmParams<T> &p, Smem &sm, unsigned int epoch)
     {
         const int g = blockIdx.x;
         T acc[TM][TN];
+        if (!TMASK && p.shared_pack) share_pack(p, sm, epoch);
         for (int t = g; t < p.dp_tiles; t += p.grid) {
             int i, j;
             tile_of(p, t, i, j);

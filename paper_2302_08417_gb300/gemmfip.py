@@ -34,6 +34,7 @@ GFIP_STATUS_BAD_PROBLEM = 0x4
 GFIP_GROUP_TILE_DEFAULT, GFIP_GROUP_TILE_SMALL = 0, 1
 
 GFIP_PACK_AUTO, GFIP_PACK_NONE, GFIP_PACK_A, GFIP_PACK_B, GFIP_PACK_BOTH = range(5)
+GFIP_PACKER_AUTO, GFIP_PACKER_LINE, GFIP_PACKER_SHARED = range(3)
 
 # exported symbol -> (restype, argtypes)
 _i64, _dbl, _flt, _ptr = ctypes.c_int64, ctypes.c_double, ctypes.c_float, ctypes.c_void_p
@@ -47,6 +48,7 @@ SIGNATURES = {
     "gfip_workspace_size": (_sz, [_ptr, _chr, _chr, _i64, _i64, _i64, _int]),
     "gfip_set_workspace": (_int, [_ptr, _ptr, _sz]),
     "gfip_set_pack_policy": (_int, [_ptr, _int]),
+    "gfip_set_packer": (_int, [_ptr, _int]),
     "gfip_dgemm": (_int, _GEMM_D),
     "gfip_sgemm": (_int, _GEMM_S),
     "gfip_dgemm_direct": (_int, _GEMM_D),
@@ -143,6 +145,10 @@ def gfip_set_workspace(handle: int, ptr: int, nbytes: int) -> int:
 
 def gfip_set_pack_policy(handle: int, policy: int) -> int:
     return load().gfip_set_pack_policy(handle, policy)
+
+
+def gfip_set_packer(handle: int, packer: int) -> int:
+    return load().gfip_set_packer(handle, packer)
 
 
 def _gemm_call(name, handle, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc):
@@ -337,6 +343,11 @@ class Handle:
         rc = gfip_set_pack_policy(self.h, policy)
         if rc != GFIP_OK:
             raise GemmError(rc, "gfip_set_pack_policy")
+
+    def set_packer(self, packer: int):
+        rc = gfip_set_packer(self.h, packer)
+        if rc != GFIP_OK:
+            raise GemmError(rc, "gfip_set_packer")
 
     def status(self) -> int:
         return gfip_get_status(self.h)

@@ -23,7 +23,7 @@ class Runner:
         self.h.bind_stream()
 
     def run(self, p: inputs.Problem, variant="fused", policy=g.GFIP_PACK_AUTO, C_init=None,
-            A_dev=None, B_dev=None, expect_rc=0):
+            A_dev=None, B_dev=None, expect_rc=0, packer=g.GFIP_PACKER_AUTO):
         """Returns (C as a flat numpy buffer without the guard, guard, A after, B after)."""
         esz = p.A.dtype.itemsize
         A = A_dev if A_dev is not None else torch.from_numpy(p.A).to(self.dev)
@@ -32,6 +32,7 @@ class Runner:
         Cbuf = np.concatenate([c0, np.full(GUARD, np.nan, dtype=c0.dtype)])
         C = torch.from_numpy(Cbuf).to(self.dev)
         self.h.set_pack_policy(policy)
+        self.h.set_packer(packer)
         self.h.ensure_workspace(p.transa, p.transb, p.m, p.n, p.k, esz)
         name = g.ENTRY[(variant, esz)]
         rc = g._gemm_call(name, self.h.h, p.transa, p.transb, p.m, p.n, p.k, p.alpha,
@@ -40,6 +41,7 @@ class Runner:
         torch.cuda.synchronize()
         out = C.cpu().numpy()
         self.h.set_pack_policy(g.GFIP_PACK_AUTO)
+        self.h.set_packer(g.GFIP_PACKER_AUTO)
         return out[: c0.size], out[c0.size:]
 
 

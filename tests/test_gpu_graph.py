@@ -24,22 +24,25 @@ def runner():
     return gu.Runner()
 
 
+LINE, SHARED = g.GFIP_PACKER_LINE, g.GFIP_PACKER_SHARED
 CASES = [
     # FP64 32 x 32 tiles: 1120 tiles over a smaller persistent grid -> packing and stream-K
-    (np.float64, "N", "N", 1100, 1000, 900, g.GFIP_PACK_AUTO),
-    (np.float64, "T", "T", 700, 650, 1300, g.GFIP_PACK_BOTH),
+    (np.float64, "N", "N", 1100, 1000, 900, g.GFIP_PACK_AUTO, LINE),
+    (np.float64, "T", "T", 700, 650, 1300, g.GFIP_PACK_BOTH, LINE),
+    (np.float64, "N", "T", 900, 1000, 800, g.GFIP_PACK_AUTO, SHARED),
     # FP32 128 x 128 tiles: 18 x 18 tiles -> one partial wave split along k
-    (np.float32, "N", "T", 2300, 2200, 700, g.GFIP_PACK_AUTO),
-    (np.float32, "T", "N", 600, 900, 2000, g.GFIP_PACK_BOTH),
+    (np.float32, "N", "T", 2300, 2200, 700, g.GFIP_PACK_AUTO, LINE),
+    (np.float32, "T", "N", 600, 900, 2000, g.GFIP_PACK_BOTH, LINE),
+    (np.float32, "N", "N", 1500, 1400, 1100, g.GFIP_PACK_AUTO, SHARED),
 ]
 
 
-@pytest.mark.parametrize("dtype,ta,tb,m,n,k,policy", CASES)
+@pytest.mark.parametrize("dtype,ta,tb,m,n,k,policy,packer", CASES)
 @pytest.mark.parametrize("variant", ["fused", "pack_then_compute"])
 def test_replayed_graph_matches_eager_and_oracle(runner, dtype, ta, tb, m, n, k, policy,
-                                                 variant):
+                                                 packer, variant):
     p = inputs.problem(m + n + k, ta, tb, m, n, k, 0.75, 0.5, 7, 3, 5, dtype=dtype)
-    eager, _ = runner.run(p, variant, policy=policy)
+    eager, _ = runner.run(p, variant, policy=policy, packer=packer)
     ref, ab = gu.reference(p)
     gu.assert_close(p, eager, ref, ab, label="eager")
 
@@ -50,6 +53,7 @@ def test_replayed_graph_matches_eager_and_oracle(runner, dtype, ta, tb, m, n, k,
     C0 = torch.from_numpy(p.C0).to(dev)
     C = C0.clone()
     h.set_pack_policy(policy)
+    h.set_packer(packer)
     h.ensure_workspace(p.transa, p.transb, p.m, p.n, p.k, esz)
     torch.cuda.synchronize()
     name = g.ENTRY[(variant, esz)]
@@ -71,7 +75,9 @@ def test_replayed_graph_matches_eager_and_oracle(runner, dtype, ta, tb, m, n, k,
             got = C.cpu().numpy()
             assert np.array_equal(got.view(np.uint8), eager.view(np.uint8)), f"replay {rep}"
         # an eager call on the same handle between replays keeps both correct
-        again, _ = runner.run(p, variant, policy=policy)
+        again, _ = runner.run(p, variant, policy=policy, packer=packer)
+        h.set_pack_policy(policy)
+        h.set_packer(packer)
         assert np.array_equal(again.view(np.uint8), eager.view(np.uint8))
         C.copy_(C0)
         graph.replay()
@@ -80,4 +86,5 @@ def test_replayed_graph_matches_eager_and_oracle(runner, dtype, ta, tb, m, n, k,
     finally:
         h.bind_stream(torch.cuda.current_stream())
         h.set_pack_policy(g.GFIP_PACK_AUTO)
+        h.set_packer(g.GFIP_PACKER_AUTO)
     assert h.status() == 0

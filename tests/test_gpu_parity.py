@@ -80,8 +80,9 @@ def test_integer_inputs_bit_exact(runner, dtype):
 
 @pytest.mark.parametrize("dtype", DTYPES, ids=["f64", "f32"])
 def test_variants_and_policies_bitwise_identical(runner, dtype):
-    """Packing changes where a tile is read from, never its value: all three variants and
-    all five pack policies give the same bits."""
+    """Packing changes where a tile is read from, never its value: all three variants, all
+    five pack policies and both packers (first tile line, shared by all CTAs) give the same
+    bits."""
     for (m, n, k), (ta, tb) in itertools.product(
             [(520, 300, 700), (96, 1100, 260), (2048, 64, 48)], itertools.product("NT", "NT")):
         p = inputs.problem(3, ta, tb, m, n, k, -1.5, 0.5, 7, 0, 7, dtype=dtype)
@@ -89,10 +90,31 @@ def test_variants_and_policies_bitwise_identical(runner, dtype):
         for variant in ("fused", "pack_then_compute"):
             got, _ = runner.run(p, variant)
             assert np.array_equal(got.view(np.uint8), base.view(np.uint8)), variant
-        for policy in (g.GFIP_PACK_NONE, g.GFIP_PACK_A, g.GFIP_PACK_B, g.GFIP_PACK_BOTH):
-            got, _ = runner.run(p, "fused", policy=policy)
-            assert np.array_equal(got.view(np.uint8), base.view(np.uint8)), policy
+        for policy, packer in itertools.product(
+                (g.GFIP_PACK_AUTO, g.GFIP_PACK_NONE, g.GFIP_PACK_A, g.GFIP_PACK_B,
+                 g.GFIP_PACK_BOTH), (g.GFIP_PACKER_LINE, g.GFIP_PACKER_SHARED)):
+            got, _ = runner.run(p, "fused", policy=policy, packer=packer)
+            assert np.array_equal(got.view(np.uint8), base.view(np.uint8)), (policy, packer)
         gu.assert_close(p, base)
+
+
+@pytest.mark.parametrize("dtype", DTYPES, ids=["f64", "f32"])
+def test_shared_packer_sizes_and_codes(runner, dtype):
+    """The shared packer on shapes whose pack units do not divide over the CTAs (fewer units
+    than CTAs, several rounds, ragged k), against the oracle and bitwise against direct;
+    an unknown packer value is refused."""
+    for (m, n, k), (ta, tb) in itertools.product(
+            [(70, 300, 33), (1000, 900, 1000), (3000, 260, 900)], (("N", "N"), ("T", "T"))):
+        p = inputs.problem(5, ta, tb, m, n, k, 0.75, 0.5, 7, 3, 7, dtype=dtype)
+        base, _ = runner.run(p, "direct")
+        got, guard = runner.run(p, "fused", policy=g.GFIP_PACK_BOTH,
+                                packer=g.GFIP_PACKER_SHARED)
+        assert np.array_equal(got.view(np.uint8), base.view(np.uint8)), (m, n, k, ta, tb)
+        gu.assert_gap_untouched(p, got, guard)
+        gu.assert_close(p, got, label="shared packer")
+        assert runner.h.status() == 0
+    assert g.gfip_set_packer(runner.h.h, 3) == g.GFIP_ERR_ARG
+    assert g.gfip_set_packer(runner.h.h, -1) == g.GFIP_ERR_ARG
 
 
 @pytest.mark.parametrize("variant", gu.VARIANTS)
