@@ -46,7 +46,7 @@ WORKLOAD = ("fp64 gemm m=n=k=8192 N/N lda=ldb=ldc=8199 alpha=1 beta=0.5 uniform[
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the FP64 GEMM
 # kernel on this workload, from a one-pass ncu capture of the full-size launch (summary in
 # profiles/); valid only while the kernel sources hash to kernel_hash.
-TRAFFIC = {"bytes_per_launch": 39.02e9 + 1.66e9, "kernel_hash": "3588d660b09817dd"}
+TRAFFIC = {"bytes_per_launch": 43.07e9 + 1.66e9, "kernel_hash": "52672c10deefe546"}
 KERNEL_SOURCES = ["paper_2302_08417_gb300/csrc/gfip_kernels.cuh",
                   "paper_2302_08417_gb300/csrc/gfip_internal.h"]
 
@@ -1015,7 +1015,9 @@ def main():
                          "d2h_bytes_per_step": g.span_bytes(hC),
                          "steps": args.e2e_steps,
                          "path": "paper_2302_08417_gb300.gemm(pinned host tensors) -> "
-                                 f"{entry}; copies and compute inside the timed region"}
+                                 f"{entry} per 1024-column block of C, uploads, blocks and "
+                                 "downloads pipelined on three streams; copies and compute "
+                                 "inside the timed region"}
         # oracle on the host cores, bounded sample of the same workload
         result["cpu_baseline"] = cpu_oracle_sample(
             bufA.numpy().reshape(-1), bufB.numpy().reshape(-1), bufC.numpy().reshape(-1),
