@@ -735,7 +735,8 @@ def trsm_report(g, torch, shapes=((8192, 8192), (2048, 2048))):
     substitution's multiply-adds), fused and raw-only, against the full GEMM of the same
     shape.  Device time of one whole solve (a diagonal solve and a GEMM update per 64-wide
     block), CUDA events, best of a few."""
-    out = {"note": "side L, uplo L, trans N, diag N, ld = m + 7; flops m^2 n; blocks of 64"}
+    out = {"note": "side L, uplo L, trans N, diag N, ld = m + 7; flops m^2 n; panels of 512 "
+                   "unknowns, blocks of 64"}
     h = g.Handle()
     h.bind_stream()
     for dtype, tag in ((torch.float64, "f64"), (torch.float32, "f32")):

@@ -220,9 +220,11 @@ int gfip_strmm(gfip_handle_t handle, char side, char uplo, char transa, char dia
  * Solves op(A) * X = alpha * B (side 'L', A m x m) or X * op(A) = alpha * B (side 'R',
  * A n x n) and overwrites B (m x n, column-major, ldb >= max(1, m)) with X; op(A), uplo,
  * diag and lda as for gfip_dtrmm (only the uplo triangle of A is read, and not its
- * diagonal for diag 'U').  Blocked: over the diagonal blocks of op(A) (64 unknowns) in solve
- * order, a substitution kernel solves the block for every right-hand side, then one fused
- * GEMM (alpha -1, beta 1) removes its contribution from the unknowns still to be solved.
+ * diagonal for diag 'U').  Blocked on two levels: over panels of 512 unknowns in solve
+ * order, and inside a panel over its diagonal blocks of 64, a substitution kernel solves the
+ * block for every right-hand side and one fused GEMM (alpha -1, beta 1) removes its
+ * contribution from the panel's unknowns still to be solved; after each panel one fused GEMM
+ * removes the panel's contribution from all other unknowns still to be solved.
  * No singularity test is made (as in the reference BLAS): a zero on a non-unit diagonal
  * gives Inf or NaN.  BLAS rules: alpha == 0 sets B to zero without reading A or B; m == 0
  * or n == 0 returns at once.  Errors as gfip_dtrmm.  Needs gfip_trsm_workspace_size() bytes

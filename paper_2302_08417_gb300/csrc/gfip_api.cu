@@ -25,6 +25,7 @@ constexpr size_t kDoneCountOffset = 128;    // header word: finished CTAs of the
 constexpr size_t kPackCountOffset = 192;    // header word: tiles packed by shared packing
 constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
 constexpr int kMinSplitRun = 8;              // shortest k run per CTA in a split wave
+constexpr int kTrsmPanel = 512;              // TRSM: unknowns per panel (two-level blocking)
 constexpr int kSharedMinRun = 16;            // AUTO packer: shared from this many k-blocks per CTA
 constexpr unsigned long long kOzakiWaitNs = 2000000000ull;  // 2 s per pipeline wait
 
@@ -587,17 +588,23 @@ int trmm_entry(gfip_handle_t handle, char side, char uplo, char transa, char dia
 template <typename T>
 size_t trsm_workspace_impl(Handle *h, char side, int64_t m, int64_t n)
 {
-    // the largest update: all of B against one block of TRSM_NB
-    const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)m, (int)n, gfip::TRSM_NB);
-    return total_bytes(h, pl);
+    // every update is at most all of B (m x n) against one panel or one block of unknowns,
+    // and its plan's workspace grows with each dimension
+    const bool left = side == 'L' || side == 'l';
+    const int na = (int)(left ? m : n);
+    const Plan<T> panel =
+        make_plan<T>(h, Variant::Fused, (int)m, (int)n, std::min(kTrsmPanel, na));
+    const Plan<T> block =
+        make_plan<T>(h, Variant::Fused, (int)m, (int)n, std::min(gfip::TRSM_NB, na));
+    return std::max(total_bytes(h, panel), total_bytes(h, block));
 }
 
 // TRSM, blocked: B := alpha B, then over the diagonal blocks of op(A) in solve order
 // (forward for a lower triangular system, backward for an upper one; for side 'R' the system
 // of each row of X is op(A)^T): solve the block's unknowns for every right-hand side
-// (trsm_diag_kernel), then subtract their contribution from the unknowns still to be solved
-// with one fused GEMM (alpha = -1, beta = 1), whose first tile line packs the block's panel
-// of X (and of op(A)) once for all later tiles.  Only the triangle of A is read.
+// (trsm_diag_kernel), then subtract their contribution from unknowns still to be solved
+// with fused GEMMs (alpha = -1, beta = 1) that pack the solved rows of X (and the panel of
+// op(A)) once for all their tiles.  Only the triangle of A is read.
 template <typename T>
 int trsm_entry(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
                int64_t n, T alpha, const T *A, int64_t lda, T *B, int64_t ldb)
@@ -612,12 +619,10 @@ int trsm_entry(gfip_handle_t handle, char side, char uplo, char transa, char dia
     if (too_big(m) || too_big(n) || too_big(lda) || too_big(ldb)) return GFIP_ERR_SIZE;
     if (B == nullptr) return GFIP_ERR_NULLPTR;
     if (alpha != T(0)) {
-        // every check before the first launch: the largest update's workspace (all of B
-        // against one block) bounds every later one
+        // every check before the first launch
         if (A == nullptr) return GFIP_ERR_NULLPTR;
         if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
-        const Plan<T> pl = make_plan<T>(h, Variant::Fused, (int)m, (int)n, gfip::TRSM_NB);
-        if (total_bytes(h, pl) > h->ws_bytes) return GFIP_ERR_WORKSPACE;
+        if (trsm_workspace_impl<T>(h, side, m, n) > h->ws_bytes) return GFIP_ERR_WORKSPACE;
     }
     if (alpha != T(1)) {   // B := alpha B (alpha == 0: zeros, B not read)
         if (gfip::launch_scale<T>(B, ldb, (int)m, (int)n, alpha, gfip::TRI_NONE, h->stream) !=
@@ -632,35 +637,48 @@ int trsm_entry(gfip_handle_t handle, char side, char uplo, char transa, char dia
     const bool lower_t = left ? lower_op : !lower_op;
     const bool unit = diag == 'U' || diag == 'u';
     const int na = (int)(left ? m : n);
-    const int nblocks = (na + gfip::TRSM_NB - 1) / gfip::TRSM_NB;
     const char ta = trans ? 'T' : 'N';
-    for (int step = 0; step < nblocks; ++step) {
-        const int kbi = lower_t ? step : nblocks - 1 - step;
-        const int k0 = kbi * gfip::TRSM_NB;
-        const int kb = std::min(gfip::TRSM_NB, na - k0);
-        // the block's unknowns: rows k0.. of B (side L) or its columns k0.. (side R)
-        cudaError_t e = left ? gfip::launch_trsm_diag<T>(B + k0, ldb, 1, (int)n, A, lda, trans,
-                                                         k0, kb, lower_t, 0, unit, h->stream)
-                             : gfip::launch_trsm_diag<T>(B + (int64_t)k0 * ldb, 1, ldb, (int)m,
-                                                         A, lda, trans, k0, kb, lower_t, 1, unit,
-                                                         h->stream);
-        if (e != cudaSuccess) return GFIP_ERR_CUDA;
-        // the unknowns still to be solved: after the block (forward) or before it (backward)
-        const int r0 = lower_t ? k0 + kb : 0, r1 = lower_t ? na : k0;
-        if (r1 <= r0) continue;
-        int rc;
+    // B[rest] -= op(A)[rest, k0:k0+kb] X[k0:k0+kb] for the unknowns r0..r1-1 (side L), or
+    // B[:, rest] -= X[:, k0:k0+kb] op(A)[k0:k0+kb, rest] (side R)
+    auto update = [&](int k0, int kb, int r0, int r1) -> int {
+        if (r1 <= r0) return GFIP_OK;
         if (left) {
-            // B[r0:r1, :] -= op(A)[r0:r1, k0:k0+kb] * X[k0:k0+kb, :]
             const T *ap = trans ? A + k0 + (int64_t)r0 * lda : A + r0 + (int64_t)k0 * lda;
-            rc = launch_plan<T>(h, Variant::Fused, gfip::TRI_NONE, ta, 'N', r1 - r0, n, kb,
-                                T(-1), ap, lda, B + k0, ldb, T(1), B + r0, ldb);
-        } else {
-            // B[:, r0:r1] -= X[:, k0:k0+kb] * op(A)[k0:k0+kb, r0:r1]
-            const T *ap = trans ? A + r0 + (int64_t)k0 * lda : A + k0 + (int64_t)r0 * lda;
-            rc = launch_plan<T>(h, Variant::Fused, gfip::TRI_NONE, 'N', ta, m, r1 - r0, kb,
-                                T(-1), B + (int64_t)k0 * ldb, ldb, ap, lda, T(1),
-                                B + (int64_t)r0 * ldb, ldb);
+            return launch_plan<T>(h, Variant::Fused, gfip::TRI_NONE, ta, 'N', r1 - r0, n, kb,
+                                  T(-1), ap, lda, B + k0, ldb, T(1), B + r0, ldb);
         }
+        const T *ap = trans ? A + r0 + (int64_t)k0 * lda : A + k0 + (int64_t)r0 * lda;
+        return launch_plan<T>(h, Variant::Fused, gfip::TRI_NONE, 'N', ta, m, r1 - r0, kb,
+                              T(-1), B + (int64_t)k0 * ldb, ldb, ap, lda, T(1),
+                              B + (int64_t)r0 * ldb, ldb);
+    };
+    // Two levels: panels of kTrsmPanel unknowns in solve order; inside a panel, blocks of
+    // TRSM_NB solved by substitution, each followed by an update of the panel's unknowns
+    // still to be solved; after the panel, one update of all unknowns outside it still to be
+    // solved (k = kTrsmPanel, long enough runs for the GEMM's pipelines, instead of one short
+    // k = TRSM_NB update of all of them per block).
+    const int npanels = (na + kTrsmPanel - 1) / kTrsmPanel;
+    for (int ps = 0; ps < npanels; ++ps) {
+        const int pi = lower_t ? ps : npanels - 1 - ps;
+        const int p0 = pi * kTrsmPanel;
+        const int pw = std::min(kTrsmPanel, na - p0);
+        const int nblocks = (pw + gfip::TRSM_NB - 1) / gfip::TRSM_NB;
+        for (int step = 0; step < nblocks; ++step) {
+            const int kbi = lower_t ? step : nblocks - 1 - step;
+            const int k0 = p0 + kbi * gfip::TRSM_NB;
+            const int kb = std::min(gfip::TRSM_NB, p0 + pw - k0);
+            // the block's unknowns: rows k0.. of B (side L) or its columns k0.. (side R)
+            cudaError_t e =
+                left ? gfip::launch_trsm_diag<T>(B + k0, ldb, 1, (int)n, A, lda, trans, k0, kb,
+                                                 lower_t, 0, unit, h->stream)
+                     : gfip::launch_trsm_diag<T>(B + (int64_t)k0 * ldb, 1, ldb, (int)m, A, lda,
+                                                 trans, k0, kb, lower_t, 1, unit, h->stream);
+            if (e != cudaSuccess) return GFIP_ERR_CUDA;
+            // the panel's unknowns still to be solved: after the block (forward) or before it
+            const int rc = lower_t ? update(k0, kb, k0 + kb, p0 + pw) : update(k0, kb, p0, k0);
+            if (rc != GFIP_OK) return rc;
+        }
+        const int rc = lower_t ? update(p0, pw, p0 + pw, na) : update(p0, pw, 0, p0);
         if (rc != GFIP_OK) return rc;
     }
     return GFIP_OK;

@@ -118,6 +118,29 @@ def test_small_and_multiblock(runner, dtype, side, uplo, ta, diag):
                                                                          m, n)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("side,uplo,ta,diag", COMBOS)
+def test_several_panels(runner, dtype, side, uplo, ta, diag):
+    """Systems of 1100 unknowns: three panels of the two-level blocking (512, 512 and a
+    ragged 76), forward and backward, against the residual bound and the oracle."""
+    rng = np.random.Generator(np.random.PCG64(25))
+    m, n = (1100, 37) if side == "L" else (37, 1100)
+    na = m if side == "L" else n
+    lda, ldb = na + 3, m + 5
+    A = system(rng, na, lda, uplo, diag, dtype)
+    B0 = inputs.colmajor(rng, m, n, ldb, dtype)
+    X, guard = run(runner, side, uplo, ta, diag, m, n, -1.25, A, lda, B0, ldb)
+    assert np.all(np.isnan(guard))
+    residual_check(side, uplo, ta, diag, m, n, -1.25, A, lda, B0, ldb, X)
+    ref = oracle.trsm_result(side, uplo, ta, diag, m, n, -1.25, A.astype(np.float64), lda,
+                             B0.astype(np.float64), ldb)
+    got = inputs.as_matrix(X.astype(np.float64), m, n, ldb)
+    want = inputs.as_matrix(ref, m, n, ldb)
+    u = inputs.unit_roundoff(A.dtype)
+    scale = np.abs(want).max(axis=0 if side == "L" else 1, keepdims=True)
+    assert np.all(np.abs(got - want) <= 64 * (na + 64) * u * scale)
+
+
 @pytest.mark.parametrize("side,uplo,ta", list(itertools.product("LR", "LU", "NT")))
 def test_integer_unit_exact_and_policies(runner, side, uplo, ta):
     """Unit systems with sparse entries in {-1, 0, 1} and small integer right-hand sides have
