@@ -413,9 +413,10 @@ struct Kernel {
     using AccT = T[TM][TN];
 
     // Decision for one operand tile at one k-block, in two steps so the ready-word load
-    // overlaps compute.  FIP: the first tile column produces A panels, the first tile row
-    // produces B panels; the others read what is already published (the whole panel, known
-    // at segment start, or this k-block's word).
+    // overlaps compute.  FIP with line producers: the first tile column produces A panels,
+    // the first tile row produces B panels; the others read what is already published (the
+    // whole panel, known at segment start, or this k-block's word).  FIP with shared packing:
+    // no producers; a panel counts as whole once the count of packed tiles is complete.
     //   need_word(): does the decision need this k-block's ready word?
     //   classify():  the decision, given that word (relaxed-loaded) when needed.
     static __device__ __forceinline__ bool need_word(int mode, bool producer, int full)
