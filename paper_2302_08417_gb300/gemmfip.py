@@ -413,6 +413,17 @@ def _span_to_device(X):
 HOST_BLOCK_COLS = 1024
 
 
+def host_blocks(n: int, transb: str) -> list[tuple[int, int]]:
+    """Column ranges [j0, j1) of C that the end-to-end path runs as separate calls: n //
+    HOST_BLOCK_COLS near-equal blocks (each at least HOST_BLOCK_COLS wide) when op(B) = B,
+    else (or below two blocks) one range.  An empty C gives one empty range."""
+    blocks = n // HOST_BLOCK_COLS if transb.upper() == "N" else 1
+    if blocks < 2:
+        return [(0, n)]
+    bounds = [n * q // blocks for q in range(blocks + 1)]
+    return list(zip(bounds[:-1], bounds[1:]))
+
+
 def _gemm_host(A, B, C_h, alpha, beta, transa, transb, variant, handle):
     """The end-to-end path: host operands in, host result out.  Each operand's storage span
     (ld*(cols-1) + rows elements) is copied as is, so leading dimensions are kept.
@@ -426,8 +437,8 @@ def _gemm_host(A, B, C_h, alpha, beta, transa, transb, variant, handle):
     copy all, one call, copy back."""
     import torch
     n = C_h.shape[1]
-    blocks = n // HOST_BLOCK_COLS if transb.upper() == "N" else 1
-    if blocks < 2 or C_h.shape[0] == 0 or B.shape[0] == 0:
+    ranges = host_blocks(n, transb)
+    if len(ranges) < 2 or C_h.shape[0] == 0 or B.shape[0] == 0:
         dA, dB, dC = (_span_to_device(X) for X in (A, B, C_h))
         gemm(dA, dB, dC, alpha, beta, transa, transb, variant, handle)
         _span(C_h).copy_(_span(dC), non_blocking=True)
@@ -442,15 +453,13 @@ def _gemm_host(A, B, C_h, alpha, beta, transa, transb, variant, handle):
     dC_flat = torch.empty(spanC.numel(), dtype=C_h.dtype, device=dev)
     ldb, ldc = _colmajor_ld(B, "B"), _colmajor_ld(C_h, "C")
     k, m = B.shape[0], C_h.shape[0]
-    bounds = [n * q // blocks for q in range(blocks + 1)]
     # C goes up when beta reads it, or when its rows m..ldc-1 lie inside a block's span
     # (they travel up and back down unchanged)
     upload_c = beta != 0.0 or ldc > m
     with torch.cuda.stream(s_in):
         dA = _span_to_device(A)
         ins = []
-        for q in range(blocks):
-            j0, j1 = bounds[q], bounds[q + 1]
+        for j0, j1 in ranges:
             b0, b1 = j0 * ldb, (j1 - 1) * ldb + k
             dB_flat[b0:b1].copy_(spanB[b0:b1], non_blocking=True)
             if upload_c:
@@ -459,8 +468,7 @@ def _gemm_host(A, B, C_h, alpha, beta, transa, transb, variant, handle):
             ev = torch.cuda.Event()
             ev.record(s_in)
             ins.append(ev)
-    for q in range(blocks):
-        j0, j1 = bounds[q], bounds[q + 1]
+    for q, (j0, j1) in enumerate(ranges):
         compute.wait_event(ins[q])
         dBq = torch.as_strided(dB_flat, (k, j1 - j0), (1, ldb), j0 * ldb)
         dCq = torch.as_strided(dC_flat, (m, j1 - j0), (1, ldc), j0 * ldc)
