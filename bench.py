@@ -825,12 +825,16 @@ def run_reference(args, world, rank):
     val = gflop(M, cols, K) / dt
     sample = (f"each step: the first {cols} of {N} columns of C (m=k={M}, lda=ldb=ldc={M+PAD},"
               f" alpha=1, beta=0.5), FP64 j-p-i triple loop, OpenMP over columns")
+    # the metric and config of this arm are those of the GPU arm on the same arguments
     print(json.dumps({
-        "impl": "reference", "metric": "fp64 gemm throughput", "value": round(val, 3),
+        "impl": "reference", "metric": f"{args.dtype} gemm throughput ({args.variant})",
+        "value": round(val, 3),
         "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K},
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K, "transa": "N", "transb": "N",
+                   "lda": lda, "ldb": ldb, "ldc": ldc, "alpha": ALPHA, "beta": BETA,
+                   "parallelism": f"host cores x{threads}"},
         "cpu_baseline": {"value": round(val, 3), "unit": "GFLOP/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(val, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
