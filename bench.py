@@ -40,8 +40,12 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_GFLOPS = SMS * DFMA_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ / 1e3   # 1258.6
 FP32_PEAK_GFLOPS = SMS * FFMA_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ / 1e3   # 80547.8
 HBM_GBS = 6785.2
-WORKLOAD = ("fp64 gemm m=n=k=8192 N/N lda=ldb=ldc=8199 alpha=1 beta=0.5 uniform[-1,1] "
-            "fused-in-packing")
+def workload(dtype="f64", size=8192, variant="fused") -> str:
+    return (f"{dtype} gemm m=n=k={size} N/N lda=ldb=ldc={size + PAD} alpha=1 beta=0.5 "
+            f"uniform[-1,1] {variant}")
+
+
+WORKLOAD = workload()
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the FP64 GEMM
 # kernel on this workload, from a one-pass ncu capture of the full-size launch (summary in
@@ -878,8 +882,7 @@ def main():
     args = ap.parse_args()
     if args.size != M or args.dtype != "f64" or args.variant != "fused":
         M = N = K = args.size
-        WORKLOAD = (f"{args.dtype} gemm m=n=k={M} N/N lda=ldb=ldc={M + PAD} alpha=1 beta=0.5 "
-                    f"uniform[-1,1] {args.variant}")
+        WORKLOAD = workload(args.dtype, M, args.variant)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup(args)
