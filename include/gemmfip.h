@@ -29,10 +29,10 @@
  *      ldc=13),
  * exactly as xerbla would report it; positive values are the GFIP_ERR_* runtime errors.
  * A negative return, or a GFIP_ERR_HANDLE / GFIP_ERR_WORKSPACE / GFIP_ERR_NULLPTR /
- * GFIP_ERR_SIZE / GFIP_ERR_ARG return, happens before anything is launched: C (B for
- * TRMM and TRSM) is unchanged.  GFIP_ERR_CUDA means a launch or copy failed; a call that
- * enqueues several kernels (pack-then-compute, TRMM, TRSM) may then have enqueued the
- * earlier ones, and the output operand is undefined.
+ * GFIP_ERR_SIZE / GFIP_ERR_ARG / GFIP_ERR_CAPTURE return, happens before anything is
+ * launched: C (B for TRMM and TRSM) is unchanged.  GFIP_ERR_CUDA means a launch or copy
+ * failed; a call that enqueues several kernels (pack-then-compute, TRMM, TRSM) may then
+ * have enqueued the earlier ones, and the output operand is undefined.
  *
  * Quick returns (reference-BLAS rules): m == 0 or n == 0, or (alpha == 0 or k == 0) and
  * beta == 1, return 0 with nothing launched; alpha == 0 or k == 0 scales C by beta
@@ -64,6 +64,10 @@ typedef struct gfip_handle_s *gfip_handle_t;
 #define GFIP_ERR_ARG 7          /* an invalid value for a non-BLAS argument                */
 #define GFIP_ERR_SCRATCH_LIMIT 8 /* gfip_dgemm_noalloc: the problem needs more scratch than
                                     GFIP_NOALLOC_SCRATCH_BYTES                               */
+#define GFIP_ERR_CAPTURE 9      /* the call would first clear control words of the workspace
+                                   (the first call after gfip_set_workspace, or a call needing
+                                   more control words than any before) while its stream is
+                                   capturing a CUDA graph; make one such call eagerly first    */
 
 /* Device status bits, reported by gfip_get_status(). */
 #define GFIP_STATUS_BAD_SEGMENT 0x1u   /* a split tile saw more partial sums than planned */
@@ -236,16 +240,6 @@ int gfip_dtrsm(gfip_handle_t handle, char side, char uplo, char transa, char dia
 int gfip_strsm(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
                int64_t n, float alpha, const float *A, int64_t lda, float *B, int64_t ldb);
 
-/* Test hook for the failure path of gfip_dgemm_ozaki (no counterpart in the paper; the
- * paper's CPU kernels have no waits).  Sets, for this handle's later gfip_dgemm_ozaki calls,
- * the budget of every pipeline wait in nanoseconds (0 restores the default, 2 s), and with
- * enable != 0 makes the first CTA withhold its first operand copy, so that its wait runs out:
- * the call then raises GFIP_STATUS_MMA_TIMEOUT, leaves that CTA's 128 x 128 tile of C
- * unwritten (every other tile is computed), waits for its own copies in flight, releases its
- * tensor memory and returns; the context stays usable.  Nothing else is affected.
- * Returns GFIP_ERR_HANDLE for an invalid handle. */
-int gfip_debug_ozaki_timeout(gfip_handle_t handle, int enable, uint64_t wait_ns);
-
 /* ---- Grouped GEMM: many independent problems of uneven sizes in one launch ----------------
  * The size-unified code path of Sec. 1 and Sec. 3 applied to a batch: for g < count,
  *     C_g := alpha[g] * op(A_g) * op(B_g) + beta[g] * C_g
@@ -301,7 +295,10 @@ const char *gfip_error_string(int code);
  * before anything is launched (square FP64 problems up to about m = n = k = 1600 fit; any
  * size fits the handle-based routines).  The first call on a device sets the array up: it
  * looks up the array's device address and clears its control words with an asynchronous
- * memset on the given stream, so make that first call before any stream capture.
+ * memset on the given stream, so make that first call before any stream capture (a call
+ * that has to clear control words while its stream is capturing returns GFIP_ERR_CAPTURE
+ * and enqueues nothing).  Every call looks the address up again, so after the device's
+ * context is destroyed and created again (cudaDeviceReset) the next call starts over.
  *
  * All calls on a device share the one array, and it keeps the last call's contents (each call
  * tags its control words, so stale contents are never mistaken for its own).  Calls that can

@@ -14,6 +14,7 @@
 #include "../../include/gemmfip.h"
 #include "gfip_grouped.h"
 #include "gfip_internal.h"
+#include "gfip_testing.h"
 
 namespace {
 
@@ -248,6 +249,24 @@ template <typename T> size_t total_bytes(Handle *h, const Plan<T> &pl)
     return ctrl + pl.data_bytes;
 }
 
+// Grows the handle's control region to `want` bytes.  The new part may hold data of earlier
+// calls, so it is cleared with a memset ordered on the handle's stream after them.  That
+// memset must not be recorded into a CUDA graph: a replay would clear the launch counter and
+// the ready words again while words of later eager calls kept their tags, so a stale word
+// could read as ready.  A call that needs the clear therefore returns GFIP_ERR_CAPTURE, with
+// nothing enqueued, when its stream is capturing.
+int grow_ctrl(Handle *h, size_t want)
+{
+    if (want <= h->ctrl_bytes) return GFIP_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) return GFIP_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return GFIP_ERR_CAPTURE;
+    if (cudaMemsetAsync(h->ws + h->ctrl_bytes, 0, want - h->ctrl_bytes, h->stream) != cudaSuccess)
+        return GFIP_ERR_CUDA;
+    h->ctrl_bytes = want;
+    return GFIP_OK;
+}
+
 bool too_big(int64_t v)
 {
     return v > std::numeric_limits<int32_t>::max();
@@ -297,15 +316,9 @@ int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t
     if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
     if (total_bytes(h, pl) > h->ws_bytes) return GFIP_ERR_WORKSPACE;
 
-    // Grow the control region if this plan needs more of it; the new part may hold data of
-    // earlier calls, so it is cleared (stream-ordered after them).
-    const size_t ctrl_want = round_up(pl.ctrl_needed, kCtrlGranule);
-    if (ctrl_want > h->ctrl_bytes) {
-        if (cudaMemsetAsync(h->ws + h->ctrl_bytes, 0, ctrl_want - h->ctrl_bytes, h->stream) !=
-            cudaSuccess)
-            return GFIP_ERR_CUDA;
-        h->ctrl_bytes = ctrl_want;
-    }
+    // Grow the control region if this plan needs more of it.
+    if (const int rc = grow_ctrl(h, round_up(pl.ctrl_needed, kCtrlGranule)); rc != GFIP_OK)
+        return rc;
 
     unsigned char *data = h->ws + h->ctrl_bytes;
     gfip::GemmParams<T> p{};
@@ -970,6 +983,9 @@ const char *gfip_error_string(int code)
     case GFIP_ERR_ARG: return "invalid argument value";
     case GFIP_ERR_SCRATCH_LIMIT:
         return "problem needs more scratch than the allocation-free routine's static array";
+    case GFIP_ERR_CAPTURE:
+        return "the call must clear control words first, which cannot happen while its stream "
+               "is capturing a CUDA graph";
     default: return "unknown error";
     }
 }
@@ -1019,12 +1035,7 @@ int gfip_dgemm_ozaki(gfip_handle_t handle, char transa, char transb, int64_t m, 
     const OzPlan o = oz_plan(m, n, k, slices);
     const size_t ctrl_want = std::max(h->ctrl_bytes, kCtrlGranule);
     if (ctrl_want + o.data_bytes > h->ws_bytes) return GFIP_ERR_WORKSPACE;
-    if (ctrl_want > h->ctrl_bytes) {
-        if (cudaMemsetAsync(h->ws + h->ctrl_bytes, 0, ctrl_want - h->ctrl_bytes, h->stream) !=
-            cudaSuccess)
-            return GFIP_ERR_CUDA;
-        h->ctrl_bytes = ctrl_want;
-    }
+    if (const int rc = grow_ctrl(h, ctrl_want); rc != GFIP_OK) return rc;
     unsigned char *data = h->ws + h->ctrl_bytes;
     gfip::OzakiParams p{};
     p.A = A;
@@ -1085,12 +1096,7 @@ int grouped_entry(gfip_handle_t handle, int count, const char *transa, const cha
     const size_t pre = round_up(((size_t)count + 1) * sizeof(int), kAlign);
     const size_t ctrl_want = std::max(h->ctrl_bytes, kCtrlGranule);
     if (ctrl_want + desc + pre > h->ws_bytes) return GFIP_ERR_WORKSPACE;
-    if (ctrl_want > h->ctrl_bytes) {
-        if (cudaMemsetAsync(h->ws + h->ctrl_bytes, 0, ctrl_want - h->ctrl_bytes, h->stream) !=
-            cudaSuccess)
-            return GFIP_ERR_CUDA;
-        h->ctrl_bytes = ctrl_want;
-    }
+    if (const int rc = grow_ctrl(h, ctrl_want); rc != GFIP_OK) return rc;
     unsigned char *data = h->ws + h->ctrl_bytes;
     gfip::GroupParams<T> gp{};
     gp.count = count;
@@ -1159,27 +1165,34 @@ struct NoAllocDevice {
 
 NoAllocDevice g_noalloc[kNoAllocMaxDevices];
 
-// Set-up for the current device, once: check the device, look up the array's device address
-// with that device current, and point the device's static handle at it.  The handle's
-// control-word region starts empty, so the first call clears it on its stream.
+// Set-up for the current device: check the device once, then on every call look up the
+// array's device address with that device current (cheap).  If the address changed -- the
+// device's context was destroyed and created again, which loads the module anew -- the
+// control words recorded as cleared belong to the old array, so the handle starts over with
+// an empty control region; the next call clears it on its stream.
 int noalloc_setup(NoAllocDevice &d, int dev)
 {
-    if (d.ready) return GFIP_OK;
-    int major = 0, minor = 0, sms = 0;
-    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return GFIP_ERR_CUDA;
-    if (!(major == 10 && minor == 3)) return GFIP_ERR_DEVICE;
+    if (!d.ready) {
+        int major = 0, minor = 0, sms = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return GFIP_ERR_CUDA;
+        if (!(major == 10 && minor == 3)) return GFIP_ERR_DEVICE;
+        d.h.device = dev;
+        d.h.sms = sms;
+        d.h.ws_bytes = GFIP_NOALLOC_SCRATCH_BYTES;
+        d.h.pack_policy = GFIP_PACK_AUTO;
+    }
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr)
         return GFIP_ERR_CUDA;
-    d.h.device = dev;
-    d.h.sms = sms;
-    d.h.ws = reinterpret_cast<unsigned char *>(ptr);
-    d.h.ws_bytes = GFIP_NOALLOC_SCRATCH_BYTES;
-    d.h.ctrl_bytes = 0;
-    d.h.pack_policy = GFIP_PACK_AUTO;
+    if (!d.ready || d.h.ws != ptr) {
+        d.h.ws = reinterpret_cast<unsigned char *>(ptr);
+        d.h.ctrl_bytes = 0;
+        d.h.bps_f64 = 0;
+        d.h.bps_f32 = 0;
+    }
     d.ready = true;
     return GFIP_OK;
 }

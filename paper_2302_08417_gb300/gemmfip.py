@@ -27,6 +27,7 @@ GFIP_ERR_DEVICE = 5
 GFIP_ERR_SIZE = 6
 GFIP_ERR_ARG = 7
 GFIP_ERR_SCRATCH_LIMIT = 8
+GFIP_ERR_CAPTURE = 9
 GFIP_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 GFIP_STATUS_BAD_SEGMENT = 0x1
 GFIP_STATUS_MMA_TIMEOUT = 0x2

@@ -40,10 +40,21 @@ def test_every_declared_symbol_is_exported(lib):
         assert name in g.SIGNATURES, f"binding lacks {name}"
 
 
+def test_test_hooks_stay_out_of_the_public_header(lib):
+    """The failure-path hook of the emulation is declared in the library's internal testing
+    header only, and the library still exports it for the GPU test."""
+    text = open(HEADER).read()
+    assert "gfip_debug" not in text
+    testing = open(os.path.join(ROOT, "paper_2302_08417_gb300", "csrc", "gfip_testing.h")).read()
+    assert "gfip_debug_ozaki_timeout(" in testing
+    assert hasattr(lib, "gfip_debug_ozaki_timeout")
+
+
 def test_error_strings(lib):
     assert g.error_string(0) == "success"
     assert "transa" in g.error_string(-1)
     assert "workspace" in g.error_string(g.GFIP_ERR_WORKSPACE)
+    assert "capturing" in g.error_string(g.GFIP_ERR_CAPTURE)
 
 
 ARGS = dict(transa="N", transb="N", m=2, n=2, k=2, alpha=1.0, A=16, lda=2, B=16, ldb=2,

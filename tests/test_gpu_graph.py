@@ -88,3 +88,56 @@ def test_replayed_graph_matches_eager_and_oracle(runner, dtype, ta, tb, m, n, k,
         h.set_pack_policy(g.GFIP_PACK_AUTO)
         h.set_packer(g.GFIP_PACKER_AUTO)
     assert h.status() == 0
+
+
+def test_first_call_under_capture_is_refused_then_capture_works(runner):
+    """The first call on a fresh workspace must clear its control words (a memset that a graph
+    replay would repeat, resetting the launch counter that tags every ready word).  Under
+    capture that call returns GFIP_ERR_CAPTURE and records nothing; once one eager call has
+    cleared them, the same call captures and replays exactly."""
+    p = inputs.problem(4242, "N", "N", 300, 280, 260, 1.0, 0.5, 7, 7, 7)
+    dev = runner.dev
+    h = g.Handle()
+    h.bind_stream()
+    h.ensure_workspace(p.transa, p.transb, p.m, p.n, p.k, 8)
+    A = torch.from_numpy(p.A).to(dev)
+    B = torch.from_numpy(p.B).to(dev)
+    C0 = torch.from_numpy(p.C0).to(dev)
+    C = C0.clone()
+    torch.cuda.synchronize()
+
+    def call():
+        return g.gfip_dgemm(h.h, p.transa, p.transb, p.m, p.n, p.k, p.alpha, A.data_ptr(),
+                            p.lda, B.data_ptr(), p.ldb, p.beta, C.data_ptr(), p.ldc)
+
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        h.bind_stream(stream)
+        with torch.cuda.graph(graph, stream=stream):
+            rc = call()
+            torch.cuda._sleep(1)     # keeps the captured graph non-empty
+    h.bind_stream()
+    assert rc == g.GFIP_ERR_CAPTURE, g.error_string(rc)
+    torch.cuda.synchronize()
+    assert torch.equal(C, C0), "a refused call must not touch C"
+    del graph
+
+    assert call() == 0            # eager: clears the control words
+    torch.cuda.synchronize()
+    eager = C.cpu().numpy()
+    ref, ab = gu.reference(p)
+    gu.assert_close(p, eager, ref, ab, label="eager after refusal")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        h.bind_stream(stream)
+        with torch.cuda.graph(graph, stream=stream):
+            rc = call()
+    h.bind_stream()
+    assert rc == 0
+    for _ in range(2):
+        C.copy_(C0)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(C.cpu().numpy().view(np.uint8), eager.view(np.uint8))
+    assert h.status() == 0
