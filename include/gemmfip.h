@@ -73,6 +73,8 @@ typedef struct gfip_handle_s *gfip_handle_t;
 #define GFIP_STATUS_BAD_SEGMENT 0x1u   /* a split tile saw more partial sums than planned */
 #define GFIP_STATUS_MMA_TIMEOUT 0x2u   /* gfip_dgemm_ozaki: a pipeline wait gave up (result invalid) */
 #define GFIP_STATUS_BAD_PROBLEM 0x4u   /* grouped GEMM: a problem had invalid arguments (skipped)  */
+#define GFIP_STATUS_WAIT_TIMEOUT 0x8u  /* FP32 GEMM: a pipeline wait of the warp-specialised tile
+                                          core gave up (result invalid)                          */
 
 /* Pack policies for gfip_set_pack_policy(). */
 #define GFIP_PACK_AUTO 0        /* Sec. 3.3 option table: pack A iff > 1 tile column, B iff > 1 tile

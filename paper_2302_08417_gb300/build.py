@@ -19,9 +19,10 @@ LIB = os.path.join(OUT, "libgemmfip.so")
 PROBE = os.path.join(OUT, "peak_probe")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-LIB_SOURCES = ["gfip_api.cu", "gfip_f64.cu", "gfip_f32.cu", "gfip_f64_tmask.cu",
+LIB_SOURCES = ["gfip_api.cu", "gfip_f64.cu", "gfip_f32.cu", "gfip_f32_ws.cu", "gfip_f64_tmask.cu",
                "gfip_f32_tmask.cu", "gfip_ozaki.cu", "gfip_grouped.cu", "gfip_trsm.cu"]
-HEADERS = ["gfip_internal.h", "gfip_kernels.cuh", "gfip_grouped.h", "gfip_testing.h"]
+HEADERS = ["gfip_internal.h", "gfip_kernels.cuh", "gfip_ws.cuh", "gfip_grouped.h",
+           "gfip_testing.h"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-I" + os.path.join(ROOT, "include")]
 # Extra nvcc arguments (e.g. "-DGFIP_F32_UNROLL=16" to override a tile parameter of

@@ -178,5 +178,9 @@ template <typename T>
 cudaError_t launch_scale(T *C, int64_t ldc, int m, int n, T beta, int tri, cudaStream_t s);
 // CTAs of the GEMM kernel that fit on one SM at once.
 template <typename T> int gemm_blocks_per_sm();
+// The warp-specialised FP32 tile core (gfip_f32_ws.cu): dense FP32 GEMMs over the whole of C
+// (no triangle, no triangular operand) with line producers or no packing.
+cudaError_t launch_ws_gemm(const GemmParams<float> &p, cudaStream_t s);
+int ws_blocks_per_sm();
 
 }  // namespace gfip

@@ -1109,6 +1109,11 @@ cudaError_t launch_gemm_mask(const GemmParams<T> &p, cudaStream_t s)
 
 template <typename T> cudaError_t launch_gemm_impl(const GemmParams<T> &p, cudaStream_t s)
 {
+    // dense FP32 GEMMs run on the warp-specialised tile core; SYRK triangles, TRMM masks and
+    // the explicit shared packer stay on this one (same micro-tile and k order: same bits)
+    if constexpr (std::is_same<T, float>::value)
+        if (p.tri == TRI_NONE && !p.tmask_a && !p.tmask_b && !p.shared_pack)
+            return launch_ws_gemm(p, s);
     if (p.a_contig_m)
         return p.b_contig_n ? launch_gemm_mask<T, true, true>(p, s)
                             : launch_gemm_mask<T, true, false>(p, s);
@@ -1135,6 +1140,8 @@ template <typename T> int gemm_blocks_per_sm_impl()
     n = std::min(n, blocks_per_sm_one<T, true, false>());
     n = std::min(n, blocks_per_sm_one<T, false, true>());
     n = std::min(n, blocks_per_sm_one<T, false, false>());
+    // FP32: the warp-specialised core runs with the same grid, hence the same split points
+    if constexpr (std::is_same<T, float>::value) n = std::min(n, ws_blocks_per_sm());
     return n;
 }
 

@@ -32,6 +32,7 @@ GFIP_NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 GFIP_STATUS_BAD_SEGMENT = 0x1
 GFIP_STATUS_MMA_TIMEOUT = 0x2
 GFIP_STATUS_BAD_PROBLEM = 0x4
+GFIP_STATUS_WAIT_TIMEOUT = 0x8
 GFIP_GROUP_TILE_DEFAULT, GFIP_GROUP_TILE_SMALL = 0, 1
 
 GFIP_PACK_AUTO, GFIP_PACK_NONE, GFIP_PACK_A, GFIP_PACK_B, GFIP_PACK_BOTH = range(5)
