@@ -181,6 +181,8 @@ template <typename T> int gemm_blocks_per_sm();
 // The warp-specialised FP32 tile core (gfip_f32_ws.cu): dense FP32 GEMMs over the whole of C
 // (no triangle, no triangular operand) with line producers or no packing.
 cudaError_t launch_ws_gemm(const GemmParams<float> &p, cudaStream_t s);
+// Its pack kernel (pack-then-compute): packed tiles in the swizzled layout it reads.
+cudaError_t launch_ws_pack(const PackParams<float> &p, cudaStream_t s);
 int ws_blocks_per_sm();
 
 }  // namespace gfip

@@ -1147,6 +1147,8 @@ template <typename T> int gemm_blocks_per_sm_impl()
 
 template <typename T> cudaError_t launch_pack_impl(const PackParams<T> &p, cudaStream_t s)
 {
+    // FP32 pack-then-compute GEMMs run on the warp-specialised core, which reads its own layout
+    if constexpr (std::is_same<T, float>::value) return launch_ws_pack(p, s);
     const int64_t blocks = (int64_t)(p.mt + p.nt) * p.kt;
     if (blocks <= 0) return cudaSuccess;
     const unsigned int nb = static_cast<unsigned int>(blocks);

@@ -6,25 +6,34 @@
 // k-block all sit in the instruction stream of the FFMA warps: the math pipe idles while the
 // warps of a CTA load and synchronise together, and a tile that reads the raw strided operand
 // costs the FFMA loop about 10 % more than one that reads a packed copy.  Here the roles are
-// split (Sec. 3.2's fused microkernel, with the "load and pack" half given its own warp):
+// split (Sec. 3.2's fused microkernel, with the "load and pack" half given warps of its own):
 //
-//   math warps: wait until a stage is full, run the FFMA2 loop over its BK rows, release
-//              the stage; accumulators, alpha/beta epilogue and the split-tile fix-up as in
-//              the shared tile core (same micro-tile, same k order, so the same bits)
-//   last warp:  producer: per k-block decides raw / packed / produce for each operand (the
-//              ready-word look-ups and acquire fences happen here), fills the stage with
-//              element copies of the raw strided operand or 128-byte bulk copies of the packed
-//              tile (the copy engine), and for a producer tile (Alg. 1: the first tile column
-//              packs A, the first tile row packs B) writes the staged tile to the packed buffer
-//              with bulk stores once it has arrived, then publishes it
+//   warps 0-3  math: wait until a stage is full, run the FFMA2 loop over its 32 k rows,
+//              release the stage; accumulators, alpha/beta epilogue and the split-tile fix-up
+//              (each C element is one FMA chain in k order, as in the shared tile core, so
+//              every variant and both tile cores give the same bits)
+//   warp 4     producer of op(A) tiles, warp 5 producer of op(B) tiles: per k-block each
+//              decides raw / packed / produce for its operand (the ready-word look-ups and
+//              acquire fences happen here), fills its half of the stage with element copies of
+//              the raw strided operand or ONE 16 KB bulk copy of the packed tile (the copy
+//              engine), and for a producer tile (Alg. 1: the first tile column packs A, the
+//              first tile row packs B) writes the staged tile to the packed buffer with one
+//              bulk store once it has arrived, then publishes it
 //
-// A stage is handed over on mbarriers: `full` completes when the producer's 32 lanes have
-// seen their element copies land (cp.async.mbarrier.arrive.noinc) and the bulk copies'
-// bytes have arrived (expect_tx); `empty` completes when all math warps are done with it.
-// The producer runs up to STAGES k-blocks ahead across tile and segment boundaries, so the
-// next tile's first loads overlap the current tile's last k-blocks.  Every wait is bounded by
-// a global-timer budget; a timeout raises GFIP_STATUS_WAIT_TIMEOUT (the result is then
-// invalid), every role stops, and the producer waits for its copies in flight before exiting.
+// Stage layout (and packed layout): a 128 x 32 operand tile is four 128-byte-wide segments
+// of x (m for A, n for B), each 32 rows (one per k) of 32 floats, rows 128 bytes apart with no
+// padding; the 16-byte chunk c of row kk is stored at chunk position c ^ (kk % 8).  The XOR
+// swizzle keeps both the raw copies (a warp writes 8 rows x 4 x, or 32 x of one row) and the
+// math warps' 16-byte fragment reads free of bank conflicts, and makes the packed tile in HBM
+// the exact 16 KB shared-memory image, moved by one bulk copy each way.
+//
+// A stage is handed over on mbarriers: `full` completes when both producers' 32 lanes have
+// seen their element copies land (cp.async.mbarrier.arrive.noinc) and the bulk copies' bytes
+// have arrived (expect_tx); `empty` completes when all math warps are done with it.  The
+// producers run up to STAGES k-blocks ahead across tile and segment boundaries, so the next
+// tile's first loads overlap the current tile's last k-blocks.  Every wait is bounded by a
+// global-timer budget; a timeout raises GFIP_STATUS_WAIT_TIMEOUT (the result is then
+// invalid), every role stops, and each producer waits for its copies in flight before exiting.
 #pragma once
 
 #include "gfip_kernels.cuh"
@@ -32,41 +41,38 @@
 namespace gfip {
 namespace ws {
 
-// Math micro-tile: NCM 16-byte chunks (4 floats each) along m by 2 along n per thread.  With
-// NCM = 4 (16 x 8) a 128 x 128 tile takes 4 math warps; two CTAs of 4 + 1 warps fit an SM
-// with up to 168 registers a thread, which the 128 accumulators need.  (8 x 8 on 8 math warps
-// would leave 96 registers a thread at two CTAs per SM, and spill.)  Every micro-tile shape
-// gives the same bits: each C element is one FMA chain in k order.
-#ifndef GFIP_WS_NCM
-#define GFIP_WS_NCM 4
-#endif
-#ifndef GFIP_WS_UNROLL
-#define GFIP_WS_UNROLL 8
-#endif
+// Math micro-tile: 16 x 8 per thread (4 chunks of 4 floats along m, 2 along n), so a
+// 128 x 128 tile takes 4 math warps.  Two CTAs of 4 + 2 warps fit an SM with 168 registers a
+// thread, which the 128 accumulators need (8 x 8 on 8 math warps would leave 96 and spill).
 struct Cfg {
-    static constexpr int BM = 128, BN = 128, BK = 32, NCM = GFIP_WS_NCM, NCN = 2;
+    static constexpr int BM = 128, BN = 128, BK = 32, NCM = 4, NCN = 2;
     static constexpr int THREADS = BM * BN / (NCM * 4 * NCN * 4);
-    static constexpr int UNROLL = GFIP_WS_UNROLL;
+    static constexpr int UNROLL = 8;
     static constexpr int STAGES = 3, MIN_BLOCKS = 2;
 };
 static_assert(Cfg::BM == TileCfg<float>::BM && Cfg::BN == TileCfg<float>::BN &&
                   Cfg::BK == TileCfg<float>::BK,
-              "the packed tiles are shared with the other FP32 kernels");
+              "the tile grid and its schedule are shared with the other FP32 kernels");
 
-constexpr int MATH_THREADS = Cfg::THREADS;
-constexpr int MATH_WARPS = MATH_THREADS / 32;
-constexpr int THREADS = MATH_THREADS + 32;
+constexpr int MATH_THREADS = Cfg::THREADS;     // 128
+constexpr int MATH_WARPS = MATH_THREADS / 32;  // 4
+constexpr int THREADS = MATH_THREADS + 64;     // + the A and B producer warps
 constexpr int STAGES = Cfg::STAGES;
+constexpr int TILE_FLOATS = 128 * 32;
+constexpr int TILE_BYTES = TILE_FLOATS * 4;    // one operand tile, packed or staged (16 KB)
 constexpr unsigned int STATUS_WAIT_TIMEOUT = 0x8u;       // mirrors GFIP_STATUS_WAIT_TIMEOUT
 constexpr unsigned long long WAIT_BUDGET_NS = 2000000000ull;
 constexpr long long WAIT_POLLS = 1ll << 40;              // the time budget ends every wait
 
-using Lay = TileLayout<float, 128, 32>;   // A and B tiles share one layout
-constexpr int TILE_BYTES = 128 * 32 * 4;  // one packed operand tile (16 KB)
+// Float offset of element (x, kk) of a tile in the swizzled layout.
+__host__ __device__ constexpr int swz(int x, int kk)
+{
+    return (x >> 5) * 1024 + kk * 32 + ((((x & 31) >> 2) ^ (kk & 7)) << 2) + (x & 3);
+}
 
-struct Smem {
-    float a[STAGES][Lay::ELEMS];
-    float b[STAGES][Lay::ELEMS];
+struct __align__(128) Smem {
+    float a[STAGES][TILE_FLOATS];
+    float b[STAGES][TILE_FLOATS];
     unsigned long long full[STAGES];
     unsigned long long empty[STAGES];
     int flag;    // split-tile fix-up: this CTA adds the partial sums
@@ -152,21 +158,21 @@ __device__ __forceinline__ void mbar_wait_drain(unsigned long long *bar, uint32_
     }
 }
 
-// 128-byte bulk copy global -> shared (copy engine), completing on an mbarrier.
-__device__ __forceinline__ void bulk_load_row(uint32_t dst, const void *src,
-                                              unsigned long long *bar)
+// Bulk copy global -> shared (copy engine), completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          unsigned long long *bar)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 128, [%2];"
-        ::"r"(dst), "l"(src), "r"(smem_addr(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
 
-// 128-byte bulk copy shared -> global, tracked in this thread's bulk async-groups.
-__device__ __forceinline__ void bulk_store_row(void *dst, uint32_t src)
+// Bulk copy shared -> global, tracked in this thread's bulk async-groups.
+__device__ __forceinline__ void bulk_store(void *dst, uint32_t src, uint32_t bytes)
 {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 128;" ::"l"(dst),
-                 "r"(src)
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(src), "r"(bytes)
                  : "memory");
 }
 
@@ -181,8 +187,7 @@ template <int N> __device__ __forceinline__ void bulk_wait()
     asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Orders this thread's generic-proxy accesses with its later (or earlier) async-proxy
-// (bulk copy) accesses of global memory.
+// Orders this thread's generic-proxy accesses with its async-proxy (bulk copy) accesses.
 __device__ __forceinline__ void fence_proxy_global()
 {
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -198,8 +203,16 @@ __device__ __forceinline__ void math_barrier()
     asm volatile("bar.sync 1, %0;" ::"n"(MATH_THREADS) : "memory");
 }
 
+// 16-byte shared-memory load at a 32-bit shared address plus a constant offset.
+template <int OFF> __device__ __forceinline__ void lds4(float *d, uint32_t addr)
+{
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+                 : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+                 : "r"(addr), "n"(OFF));
+}
+
 // The segments one CTA runs, in order: whole tiles of the data-parallel waves, then its share
-// of the k-split tiles.  Both roles walk the same sequence with their own cursor.
+// of the k-split tiles.  Every role walks the same sequence with its own cursor.
 struct Segment {
     int t, i, j, kb0, kb1;
     int slot;   // which of the CTA's two partial-sum slots a split segment uses
@@ -243,13 +256,14 @@ struct SegCursor {
     }
 };
 
-// Element copies of one raw 128 x 32 operand tile by the 32 producer lanes; element (x, kk)
-// of the tile at (x0, k0) of op(X) sits at g[(x0+x) + (k0+kk)*ld] (CONTIG) or
+// Element copies of one raw 128 x 32 operand tile by 32 lanes into the swizzled layout;
+// element (x, kk) of the tile at (x0, k0) of op(X) sits at g[(x0+x) + (k0+kk)*ld] (CONTIG) or
 // g[(k0+kk) + (x0+x)*ld].  Out-of-range elements are zero-filled (Sec. 2.2).
-//   CONTIG: lane covers x = lane + 32 q: a copy instruction reads 128 contiguous bytes and
-//           writes 32 consecutive words of one shared-memory row (conflict free).
+//   CONTIG: lane covers x = lane + 32 q: one copy instruction reads 128 contiguous bytes of
+//           a column and writes 32 distinct banks of one row.
 //   else:   lane covers kk = lane % 8 + 8 r, x = lane / 8 + 4 q: four 32-byte runs along k,
-//           written to 32 distinct banks thanks to the padded row pitch.
+//           written to 8 rows whose swizzled chunks fall in distinct banks.
+// A tile that lies wholly inside the operand takes the copies without per-element checks.
 template <bool CONTIG>
 __device__ __forceinline__ void raw_tile(uint32_t sdst, const float *g, int64_t ld, int x0,
                                          int k0, int x_ext, int kleft, int lane)
@@ -257,228 +271,251 @@ __device__ __forceinline__ void raw_tile(uint32_t sdst, const float *g, int64_t 
     const bool whole = (x0 + 128 <= x_ext) && (kleft >= 32);
     if (CONTIG) {
         const float *src = g + (int64_t)(x0 + lane) + (int64_t)k0 * ld;
-        uint32_t d = sdst + lane * 4;
-        uint32_t xok = 0;
+        // row kk: chunk lane/4 goes to chunk (lane/4) ^ (kk % 8); bytes within it lane % 4
+        const uint32_t rowbase = sdst + (lane & 3) * 4;
+        if (whole) {
+#pragma unroll 8
+            for (int kk = 0; kk < 32; ++kk) {
+                const uint32_t d = rowbase + kk * 128 + ((((lane >> 2) ^ (kk & 7))) << 4);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (x0 + lane + 32 * q < x_ext) xok |= 1u << q;
-#pragma unroll 4
-        for (int kk = 0; kk < 32; ++kk) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const bool ok = whole || (((xok >> q) & 1u) && kk < kleft);
-                cp_async_elem<4>(d + q * Lay::SEG * 4, ok ? src + 32 * q : g, ok);
+                for (int q = 0; q < 4; ++q) cp_async_elem<4>(d + q * 4096, src + 32 * q, true);
+                src += ld;
             }
-            src += ld;
-            d += Lay::P * 4;
+        } else {
+            uint32_t xok = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (x0 + lane + 32 * q < x_ext) xok |= 1u << q;
+#pragma unroll 4
+            for (int kk = 0; kk < 32; ++kk) {
+                const uint32_t d = rowbase + kk * 128 + ((((lane >> 2) ^ (kk & 7))) << 4);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool ok = ((xok >> q) & 1u) && kk < kleft;
+                    cp_async_elem<4>(d + q * 4096, ok ? src + 32 * q : g, ok);
+                }
+                src += ld;
+            }
         }
     } else {
         const int kl = lane & 7, xl = lane >> 3;
         const float *src = g + (int64_t)(k0 + kl) + (int64_t)(x0 + xl) * ld;
         const int64_t step = 4 * ld;
-#pragma unroll 4
-        for (int q = 0; q < 32; ++q) {
-            const int x = xl + 4 * q;
-            const uint32_t d = sdst + ((x >> 5) * Lay::SEG + (x & 31) + kl * Lay::P) * 4;
-            const bool xin = x0 + x < x_ext;
+        // element (xl + 4 q, kl + 8 r): segment q / 8, row kl + 8 r, chunk (q % 8) ^ kl, word xl
+        const uint32_t base = sdst + (kl * 32 + xl) * 4;
+        if (whole) {
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) {
+                const uint32_t d = base + (q >> 3) * 4096 + (((q & 7) ^ kl) << 4);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const bool ok = whole || (xin && kl + 8 * r < kleft);
-                cp_async_elem<4>(d + 8 * r * Lay::P * 4, ok ? src + 8 * r : g, ok);
+                for (int r = 0; r < 4; ++r) cp_async_elem<4>(d + r * 1024, src + 8 * r, true);
+                src += step;
             }
-            src += step;
+        } else {
+#pragma unroll 4
+            for (int q = 0; q < 32; ++q) {
+                const uint32_t d = base + (q >> 3) * 4096 + (((q & 7) ^ kl) << 4);
+                const bool xin = x0 + xl + 4 * q < x_ext;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const bool ok = xin && kl + 8 * r < kleft;
+                    cp_async_elem<4>(d + r * 1024, ok ? src + 8 * r : g, ok);
+                }
+                src += step;
+            }
         }
     }
 }
 
-// Bulk copies of one packed tile (128 rows of 128 bytes) into the padded stage layout; lane
-// takes rows lane + 32 q, i.e. 128-byte segment q, k row `lane`.
-__device__ __forceinline__ void packed_tile(uint32_t sdst, const float *tile, int lane,
-                                            unsigned long long *bar)
-{
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        bulk_load_row(sdst + (q * Lay::SEG + lane * Lay::P) * 4, tile + (q * 32 + lane) * 32, bar);
-}
-
-// Bulk stores of a staged tile into its packed slot (the fused pack store).
-__device__ __forceinline__ void store_tile(float *tile, uint32_t ssrc, int lane)
-{
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        bulk_store_row(tile + (q * 32 + lane) * 32, ssrc + (q * Lay::SEG + lane * Lay::P) * 4);
-}
-
 template <bool ACONTIG, bool BCONTIG> struct WsKernel {
-    using K = Kernel<float, ACONTIG, BCONTIG, Cfg>;   // micro-tile, epilogue, split fix-up math
-    static constexpr int TM = K::TM, TN = K::TN, TX = K::TX, NCM = K::NCM;
+    using K = Kernel<float, ACONTIG, BCONTIG, Cfg>;   // FFMA2 micro-tile update, split bookkeeping
+    static constexpr int TM = K::TM, TN = K::TN, TX = K::TX, NCM = K::NCM, NCN = K::NCN;
+    static_assert(TM == 16 && TN == 8 && TX == 8, "fragment addressing assumes 16 x 8 on 8 x 16");
 
-    // What the producer did with one stage: which operand tiles it must pack and publish.
+    // What a producer did with one stage of its operand.
     struct Meta {
-        int prod;      // bit 0: pack A, bit 1: pack B
-        int i, j, kb;
-        int last;      // bit 0 (1): kb ends a whole A (B) panel this CTA produced
+        int prod;     // this stage's tile is to be packed and published
+        int panel, kb;
+        int last;     // kb ends a whole panel this CTA produced
     };
 
-    static __device__ __forceinline__ float *pack_slot_a(const GemmParams<float> &p, int i, int kb)
+    // ---- producer warps ------------------------------------------------------------------
+    // OPB: false = the op(A) producer (warp 4), true = the op(B) producer (warp 5).
+    template <bool OPB> static __device__ void producer(const GemmParams<float> &p, Smem &sm)
     {
-        return p.pack_a + ((int64_t)i * p.kt + kb) * (128 * 32);
-    }
-    static __device__ __forceinline__ float *pack_slot_b(const GemmParams<float> &p, int j, int kb)
-    {
-        return p.pack_b + ((int64_t)j * p.kt + kb) * (128 * 32);
-    }
-
-    // Publishes the packed tiles of one stage (lane 0, after every lane's bulk stores of it
-    // have completed and each lane has fenced the async proxy): ready words per k-block, and
-    // the panel words when a whole panel is done.
-    static __device__ __forceinline__ void publish_meta(const GemmParams<float> &p, const Meta &m,
-                                                        unsigned int epoch)
-    {
-        if (!m.prod) return;
-        if (m.prod & 1) publish(p.state_a + (int64_t)m.i * p.kt + m.kb, epoch);
-        if (m.prod & 2) publish(p.state_b + (int64_t)m.j * p.kt + m.kb, epoch);
-        if (m.last & 1) publish(p.state_a + (int64_t)p.mt * p.kt + m.i, epoch);
-        if (m.last & 2) publish(p.state_b + (int64_t)p.nt * p.kt + m.j, epoch);
-    }
-
-    static __device__ void producer(const GemmParams<float> &p, Smem &sm)
-    {
+        constexpr bool CONTIG = OPB ? BCONTIG : ACONTIG;
         const int lane = threadIdx.x & 31;
+        const int mode = OPB ? p.mode_b : p.mode_a;
+        const float *X = OPB ? p.B : p.A;
+        const int64_t ld = OPB ? p.ldb : p.lda;
+        const int x_ext = OPB ? p.n : p.m;
+        const int npanels = OPB ? p.nt : p.mt;
+        unsigned long long *state = OPB ? p.state_b : p.state_a;
+        float *pack = OPB ? p.pack_b : p.pack_a;
+        const bool produces = OPB ? p.b_produces : p.a_produces;
+
         unsigned int epoch = 0u;
         if (lane == 0) epoch = *(volatile unsigned int *)p.launch_count + 1u;
-        epoch = __shfl_sync(0xffffffffu, epoch, 0);
-        const unsigned long long ready = ready_value(epoch);
+        const unsigned long long ready = ready_value(epoch);   // meaningful in lane 0 only
         Meta meta[STAGES];
         long long q = 0;          // k-blocks filled so far (stage q % STAGES)
         bool ok = true;
 
-        // the stage of k-block `d` has arrived: write its packed tiles (bulk stores)
+        auto buf = [&](int st) -> uint32_t {
+            return smem_addr(OPB ? sm.b[st] : sm.a[st]);
+        };
+        auto slot = [&](int panel, int kb) -> float * {
+            return pack + ((int64_t)panel * p.kt + kb) * TILE_FLOATS;
+        };
+        // lane 0: once the stage of k-block d has arrived, write its packed tile (one bulk
+        // store); one bulk group is committed per k-block, empty when nothing is packed
         auto store_stage = [&](long long d) {
             const Meta &m = meta[d % STAGES];
+            const int st = static_cast<int>(d % STAGES);
             if (m.prod) {
-                const int st = static_cast<int>(d % STAGES);
                 if (!mbar_wait(&sm.full[st], static_cast<uint32_t>((d / STAGES) & 1), sm,
                                p.status)) {
                     ok = false;
                     return;
                 }
                 fence_proxy_shared();
-                if (m.prod & 1) store_tile(pack_slot_a(p, m.i, m.kb), smem_addr(sm.a[st]), lane);
-                if (m.prod & 2) store_tile(pack_slot_b(p, m.j, m.kb), smem_addr(sm.b[st]), lane);
+                bulk_store(slot(m.panel, m.kb), buf(st), TILE_BYTES);
             }
-            bulk_commit();   // one group per k-block (empty when nothing is packed)
+            bulk_commit();
+        };
+        // lane 0: the packed tile of a stage whose bulk store has completed becomes visible
+        auto publish_meta = [&](const Meta &m) {
+            if (!m.prod) return;
+            publish(state + (int64_t)m.panel * p.kt + m.kb, epoch);
+            if (m.last) publish(state + (int64_t)npanels * p.kt + m.panel, epoch);
         };
 
         SegCursor cur;
         cur.start(p);
         Segment sg;
         while (ok && !aborted(sm) && cur.next(p, sg)) {
-            const int i = sg.i, j = sg.j, kb0 = sg.kb0, kb1 = sg.kb1;
-            const bool prod_a = p.mode_a == MODE_FIP && j == 0 && p.a_produces;
-            const bool prod_b = p.mode_b == MODE_FIP && i == 0 && p.b_produces;
+            const int panel = OPB ? sg.j : sg.i;
+            const int other = OPB ? sg.i : sg.j;
+            const bool prod = mode == MODE_FIP && other == 0 && produces;
             // a panel its producer finished whole needs no per-k-block look-ups
-            bool full_a = false, full_b = false;
-            if (lane == 0) {
-                full_a = p.mode_a == MODE_FIP && !prod_a &&
-                         ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) == ready;
-                full_b = p.mode_b == MODE_FIP && !prod_b &&
-                         ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) == ready;
+            bool full = false;
+            if (lane == 0 && mode == MODE_FIP && !prod) {
+                full = ld_relaxed(state + (int64_t)npanels * p.kt + panel) == ready;
+                if (full) {
+                    fence_acquire();
+                    fence_proxy_global();
+                }
             }
-            full_a = __shfl_sync(0xffffffffu, full_a, 0);
-            full_b = __shfl_sync(0xffffffffu, full_b, 0);
-            if (full_a || full_b) {
-                fence_acquire();
-                fence_proxy_global();
-            }
-            for (int kb = kb0; kb < kb1; ++kb) {
+            for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
                 const int st = static_cast<int>(q % STAGES);
-                if (q >= STAGES) {
-                    // the stage's previous k-block is done: math released it, and its pack
-                    // stores (issued a k-block after it arrived) have been read; publish them
-                    if (!mbar_wait(&sm.empty[st], static_cast<uint32_t>(((q / STAGES) - 1) & 1),
-                                   sm, p.status)) {
-                        ok = false;
-                        break;
-                    }
+                if (q >= STAGES &&
+                    !mbar_wait(&sm.empty[st], static_cast<uint32_t>(((q / STAGES) - 1) & 1), sm,
+                               p.status)) {
+                    ok = false;
+                    break;
                 }
-                // decisions (Sec. 3.2's four cases, per operand)
-                int da = 0, db = 0;   // 0 raw, 1 packed, 2 produce
+                // decision (Sec. 3.2's cases, for this operand): 0 raw, 1 packed, 2 produce
+                int d = 0;
                 if (lane == 0) {
-                    da = (p.mode_a == MODE_PACKED) ? 1 : 0;
-                    db = (p.mode_b == MODE_PACKED) ? 1 : 0;
-                    bool acq = false;
-                    if (p.mode_a == MODE_FIP) {
-                        if (prod_a) da = 2;
-                        else if (full_a) da = 1;
-                        else if (ld_relaxed(p.state_a + (int64_t)i * p.kt + kb) == ready) {
-                            da = 1;
-                            acq = true;
+                    if (mode == MODE_PACKED) {
+                        d = 1;
+                    } else if (mode == MODE_FIP) {
+                        if (prod) {
+                            d = 2;
+                        } else if (full) {
+                            d = 1;
+                        } else if (ld_relaxed(state + (int64_t)panel * p.kt + kb) == ready) {
+                            d = 1;
+                            fence_acquire();
+                            fence_proxy_global();
                         }
                     }
-                    if (p.mode_b == MODE_FIP) {
-                        if (prod_b) db = 2;
-                        else if (full_b) db = 1;
-                        else if (ld_relaxed(p.state_b + (int64_t)j * p.kt + kb) == ready) {
-                            db = 1;
-                            acq = true;
-                        }
-                    }
-                    if (acq) {
-                        fence_acquire();
-                        fence_proxy_global();
-                    }
-                    // copy-engine bytes this stage waits for, with this lane's arrival
-                    mbar_arrive_expect_tx(&sm.full[st], (da == 1 ? TILE_BYTES : 0) +
-                                                            (db == 1 ? TILE_BYTES : 0));
+                    // this lane's arrival, with the copy-engine bytes the stage waits for
+                    mbar_arrive_expect_tx(&sm.full[st], d == 1 ? TILE_BYTES : 0);
+                    if (d == 1) bulk_load(buf(st), slot(panel, kb), TILE_BYTES, &sm.full[st]);
                 }
-                da = __shfl_sync(0xffffffffu, da, 0);
-                db = __shfl_sync(0xffffffffu, db, 0);
-                const int kleft = p.k - kb * 32;
-                const uint32_t sa = smem_addr(sm.a[st]), sb = smem_addr(sm.b[st]);
-                if (da == 1)
-                    packed_tile(sa, pack_slot_a(p, i, kb), lane, &sm.full[st]);
-                else
-                    raw_tile<ACONTIG>(sa, p.A, p.lda, i * 128, kb * 32, p.m, kleft, lane);
-                if (db == 1)
-                    packed_tile(sb, pack_slot_b(p, j, kb), lane, &sm.full[st]);
-                else
-                    raw_tile<BCONTIG>(sb, p.B, p.ldb, j * 128, kb * 32, p.n, kleft, lane);
+                d = __shfl_sync(0xffffffffu, d, 0);
+                if (d != 1)
+                    raw_tile<CONTIG>(buf(st), X, ld, panel * 128, kb * 32, x_ext, p.k - kb * 32,
+                                     lane);
                 cp_async_arrive(&sm.full[st]);
                 Meta &m = meta[st];
-                m.prod = (da == 2 ? 1 : 0) | (db == 2 ? 2 : 0);
-                m.i = i;
-                m.j = j;
+                m.prod = (d == 2);
+                m.panel = panel;
                 m.kb = kb;
-                m.last = (kb == kb1 - 1 && kb0 == 0 && kb1 == p.kt) ? m.prod : 0;
+                m.last = (d == 2) && kb == sg.kb1 - 1 && sg.kb0 == 0 && sg.kb1 == p.kt;
                 // the previous k-block has had a k-block's time to arrive: pack it now; then
-                // every group but the newest has completed, so the k-block before it (whose
-                // stage is the next to be refilled) is published
-                if (q >= 1) {
+                // every bulk group but the newest has completed, so the k-block before it
+                // (whose stage is the next to be refilled) is published
+                if (q >= 1 && lane == 0) {
                     store_stage(q - 1);
-                    if (!ok) break;
-                    bulk_wait<1>();
-                    fence_proxy_global();
-                    __syncwarp();
-                    if (q >= 2 && lane == 0) publish_meta(p, meta[(q - 2) % STAGES], epoch);
+                    if (ok) {
+                        bulk_wait<1>();
+                        fence_proxy_global();
+                        if (q >= 2) publish_meta(meta[(q - 2) % STAGES]);
+                    }
                 }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
                 ++q;
             }
         }
-        // the last k-block's pack stores, then everything published
-        if (ok && q >= 1 && !aborted(sm)) store_stage(q - 1);
-        bulk_wait<0>();
-        fence_proxy_global();
-        __syncwarp();
-        if (ok && !aborted(sm) && lane == 0) {
-            if (q >= 2) publish_meta(p, meta[(q - 2) % STAGES], epoch);
-            if (q >= 1) publish_meta(p, meta[(q - 1) % STAGES], epoch);
+        if (lane == 0) {
+            if (ok && q >= 1 && !aborted(sm)) store_stage(q - 1);
+            bulk_wait<0>();
+            fence_proxy_global();
+            if (ok && !aborted(sm)) {
+                if (q >= 2) publish_meta(meta[(q - 2) % STAGES]);
+                if (q >= 1) publish_meta(meta[(q - 1) % STAGES]);
+            }
         }
+        __syncwarp();
         if (aborted(sm)) {
             // nothing may still write shared memory when the CTA exits
             asm volatile("cp.async.wait_all;" ::: "memory");
-            for (long long d = q - 1; d >= 0 && d >= q - STAGES; --d)
-                mbar_wait_drain(&sm.full[d % STAGES], static_cast<uint32_t>((d / STAGES) & 1));
+            if (lane == 0)
+                for (long long d = q - 1; d >= 0 && d >= q - STAGES; --d)
+                    mbar_wait_drain(&sm.full[d % STAGES], static_cast<uint32_t>((d / STAGES) & 1));
+        }
+    }
+
+    // ---- math warps ------------------------------------------------------------------------
+    // acc += A^T B over the 32 k rows of one stage.  Thread (tx, ty): A chunks c = 0..3 in
+    // segment c, chunk position tx; B chunks c = 0..1 in segment ty / 8 + 2 c, chunk position
+    // ty % 8.  In row kk the chunk position is XORed with kk % 8, which only touches address
+    // bits 4-6 (rows are 128 bytes, segments 4 KB): one XOR per operand per row.
+    // Row U (0..7) of an 8-row group whose row 0 is at ra / rb (chunk bits = tx, ty % 8).
+    template <int U>
+    static __device__ __forceinline__ void krow(uint32_t ra, uint32_t rb, float (&acc)[TM][TN])
+    {
+        const uint32_t xa = ra ^ (U << 4), xb = rb ^ (U << 4);
+        float a[TM], b[TN];
+        lds4<0 * 4096 + U * 128>(a + 0, xa);
+        lds4<1 * 4096 + U * 128>(a + 4, xa);
+        lds4<2 * 4096 + U * 128>(a + 8, xa);
+        lds4<3 * 4096 + U * 128>(a + 12, xa);
+        lds4<0 * 8192 + U * 128>(b + 0, xb);
+        lds4<1 * 8192 + U * 128>(b + 4, xb);
+        K::template fma_block<TM>(a, b, acc);
+    }
+
+    static __device__ __forceinline__ void compute(uint32_t sa, uint32_t sb, float (&acc)[TM][TN],
+                                                   int tx, int ty)
+    {
+        uint32_t ra = sa + tx * 16;
+        uint32_t rb = sb + (ty >> 3) * 4096 + (ty & 7) * 16;
+#pragma unroll 1
+        for (int k0 = 0; k0 < 32; k0 += 8) {
+            krow<0>(ra, rb, acc);
+            krow<1>(ra, rb, acc);
+            krow<2>(ra, rb, acc);
+            krow<3>(ra, rb, acc);
+            krow<4>(ra, rb, acc);
+            krow<5>(ra, rb, acc);
+            krow<6>(ra, rb, acc);
+            krow<7>(ra, rb, acc);
+            ra += 8 * 128;
+            rb += 8 * 128;
         }
     }
 
@@ -494,7 +531,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         const bool read_c = (p.beta != 0.f);
 #pragma unroll
         for (int jj = 0; jj < TN; ++jj) {
-            const int col = j * 128 + ty * CH + (jj % CH) + (jj / CH) * (128 / K::NCN);
+            const int col = j * 128 + ty * CH + (jj % CH) + (jj / CH) * (128 / NCN);
             if (col >= p.n) continue;
             float *ccol = p.C + (int64_t)col * p.ldc;
 #pragma unroll
@@ -584,13 +621,13 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         Segment sg;
         bool ok = true;
         while (ok && cur.next(p, sg)) {
-            const int i = sg.i, j = sg.j, kb0 = sg.kb0, kb1 = sg.kb1;
+            const int i = sg.i, j = sg.j;
 #pragma unroll
             for (int ii = 0; ii < TM; ++ii)
 #pragma unroll
                 for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = 0.f;
             // the segment that ends the tile's k loop will read C: warm L2 with it now
-            if (kb1 == p.kt && p.beta != 0.f) {
+            if (sg.kb1 == p.kt && p.beta != 0.f) {
                 constexpr int PER_COL = 128 / 32;
                 for (int e = tid; e < 128 * PER_COL; e += MATH_THREADS) {
                     const int col = j * 128 + e / PER_COL, row = i * 128 + (e % PER_COL) * 32;
@@ -599,12 +636,12 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
                                                                        (int64_t)col * p.ldc));
                 }
             }
-            for (int kb = kb0; kb < kb1; ++kb) {
+            for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
                 if (!mbar_wait(&sm.full[st], ph, sm, p.status)) {
                     ok = false;
                     break;
                 }
-                K::template compute<NCM>(sm.a[st], sm.b[st], acc, tx, ty, 32);
+                compute(smem_addr(sm.a[st]), smem_addr(sm.b[st]), acc, tx, ty);
                 __syncwarp();
                 if ((tid & 31) == 0) mbar_arrive(&sm.empty[st]);
                 if (++st == STAGES) {
@@ -613,7 +650,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
                 }
             }
             if (!ok) break;
-            if (kb0 == 0 && kb1 == p.kt)
+            if (sg.kb0 == 0 && sg.kb1 == p.kt)
                 epilogue(p, i, j, acc);
             else
                 fixup(p, sm, sg.t, i, j, sg.slot, acc, epoch);
@@ -631,7 +668,7 @@ __global__ void __launch_bounds__(THREADS, 2) ws_gemm_kernel(const GemmParams<fl
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&sm.full[s], 33);             // 32 lanes' copy arrivals + expect_tx
+            mbar_init(&sm.full[s], 2 * 33);   // per producer: 32 lanes' copies + expect_tx
             mbar_init(&sm.empty[s], MATH_WARPS);
         }
         sm.abort = 0;
@@ -639,7 +676,9 @@ __global__ void __launch_bounds__(THREADS, 2) ws_gemm_kernel(const GemmParams<fl
     }
     __syncthreads();
     if (warp == MATH_WARPS)
-        WsKernel<ACONTIG, BCONTIG>::producer(p, sm);
+        WsKernel<ACONTIG, BCONTIG>::template producer<false>(p, sm);
+    else if (warp == MATH_WARPS + 1)
+        WsKernel<ACONTIG, BCONTIG>::template producer<true>(p, sm);
     else
         WsKernel<ACONTIG, BCONTIG>::math(p, sm);
     __syncthreads();
@@ -654,10 +693,48 @@ __global__ void __launch_bounds__(THREADS, 2) ws_gemm_kernel(const GemmParams<fl
     }
 }
 
+// Pack kernel of the pack-then-compute variant for this tile core: one warp per (panel,
+// k-block) tile, A tiles first; raw copies into shared memory in the swizzled layout, then
+// the 16 KB image to the packed buffer with 16-byte stores.
+constexpr int PACK_WARPS = 4;
+
+template <bool ACONTIG, bool BCONTIG>
+__global__ void __launch_bounds__(PACK_WARPS * 32) ws_pack_kernel(const PackParams<float> p)
+{
+    extern __shared__ __align__(128) unsigned char pack_smem[];
+    float (*tile)[TILE_FLOATS] = reinterpret_cast<float (*)[TILE_FLOATS]>(pack_smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t a_tiles = (int64_t)p.mt * p.kt;
+    const int64_t total = a_tiles + (int64_t)p.nt * p.kt;
+    const int64_t b = (int64_t)blockIdx.x * PACK_WARPS + warp;
+    if (b >= total) return;
+    float *dst;
+    const uint32_t s = smem_addr(tile[warp]);
+    if (b < a_tiles) {
+        const int i = static_cast<int>(b / p.kt), kb = static_cast<int>(b % p.kt);
+        raw_tile<ACONTIG>(s, p.A, p.lda, i * 128, kb * 32, p.m, p.k - kb * 32, lane);
+        dst = p.pack_a + b * TILE_FLOATS;
+    } else {
+        const int64_t bb = b - a_tiles;
+        const int j = static_cast<int>(bb / p.kt), kb = static_cast<int>(bb % p.kt);
+        raw_tile<BCONTIG>(s, p.B, p.ldb, j * 128, kb * 32, p.n, p.k - kb * 32, lane);
+        dst = p.pack_b + bb * TILE_FLOATS;
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    const uint4 *src = reinterpret_cast<const uint4 *>(tile[warp]);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll 8
+    for (int c = lane; c < TILE_BYTES / 16; c += 32) __stcg(d + c, src[c]);
+}
+
 inline size_t smem_bytes()
 {
     return sizeof(Smem);
 }
+
+constexpr size_t PACK_SMEM = (size_t)PACK_WARPS * TILE_BYTES;
 
 template <bool AC, bool BC> cudaError_t configure()
 {
@@ -666,6 +743,10 @@ template <bool AC, bool BC> cudaError_t configure()
     cudaError_t e = cudaFuncSetAttribute(ws_gemm_kernel<AC, BC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem_bytes()));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_pack_kernel<AC, BC>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(PACK_SMEM));
     if (e == cudaSuccess) configured = true;
     return e;
 }
@@ -675,6 +756,17 @@ template <bool AC, bool BC> cudaError_t launch_t(const GemmParams<float> &p, cud
     cudaError_t e = configure<AC, BC>();
     if (e != cudaSuccess) return e;
     ws_gemm_kernel<AC, BC><<<p.grid, THREADS, smem_bytes(), s>>>(p);
+    return cudaGetLastError();
+}
+
+template <bool AC, bool BC> cudaError_t launch_pack_t(const PackParams<float> &p, cudaStream_t s)
+{
+    const int64_t tiles = (int64_t)(p.mt + p.nt) * p.kt;
+    if (tiles <= 0) return cudaSuccess;
+    cudaError_t e = configure<AC, BC>();
+    if (e != cudaSuccess) return e;
+    const unsigned int blocks = static_cast<unsigned int>((tiles + PACK_WARPS - 1) / PACK_WARPS);
+    ws_pack_kernel<AC, BC><<<blocks, PACK_WARPS * 32, PACK_SMEM, s>>>(p);
     return cudaGetLastError();
 }
 
