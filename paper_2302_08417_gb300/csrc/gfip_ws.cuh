@@ -552,11 +552,68 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         }
     }
 
-    // Split-tile fix-up (as in the shared tile core, with the math warps' named barrier).
-    static __device__ void fixup(const GemmParams<float> &p, Smem &sm, int t, int i, int j,
-                                 int slot, float (&acc)[TM][TN], unsigned int epoch)
+    // The last CTA of a split tile: adds the segments' partial-sum tiles in k order and
+    // applies the epilogue.  Kept out of line: the accumulators are dead here, and the sums
+    // in flight get the registers to themselves.
+    static __device__ __noinline__ void reduce_split_tile(const GemmParams<float> &p, int i, int j,
+                                                          int u, int g0, int g1)
     {
         const int tid = threadIdx.x;
+        const int64_t S = p.sk_iters;
+        const int G = p.grid;
+        // float4 f = tid + 128 r (r = 0..31) of the tile: column f / 32, rows 4 (f % 32)
+        constexpr int HALF = 16;
+        const bool read_c = (p.beta != 0.f);
+#pragma unroll 1
+        for (int r0 = 0; r0 < 32; r0 += HALF) {
+            float4 sum[HALF];
+            for (int gs = g0; gs <= g1; ++gs) {
+                const int64_t lo = S * gs / G;
+                const int gslot = (lo / p.kt == u) ? 0 : 1;
+                const float4 *src = reinterpret_cast<const float4 *>(
+                    p.partial + (int64_t)(2 * gs + gslot) * (128 * 128));
+                float4 v[HALF];
+#pragma unroll
+                for (int r = 0; r < HALF; ++r) v[r] = __ldcg(src + tid + 128 * (r0 + r));
+#pragma unroll
+                for (int r = 0; r < HALF; ++r) {
+                    if (gs == g0) {
+                        sum[r] = v[r];
+                    } else {
+                        sum[r].x += v[r].x;
+                        sum[r].y += v[r].y;
+                        sum[r].z += v[r].z;
+                        sum[r].w += v[r].w;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < HALF; ++r) {
+                const int f = tid + 128 * (r0 + r);
+                const int col = j * 128 + f / 32, row0 = i * 128 + 4 * (f % 32);
+                if (col >= p.n) continue;
+                float *ccol = p.C + (int64_t)col * p.ldc;
+                const float sv[4] = {sum[r].x, sum[r].y, sum[r].z, sum[r].w};
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    if (row0 + w >= p.m) continue;
+                    float v = p.alpha * sv[w];
+                    if (read_c) v = fmaf(p.beta, ccol[row0 + w], v);
+                    ccol[row0 + w] = v;
+                }
+            }
+        }
+    }
+
+    // Split-tile fix-up.  Every segment stores its partial sums as a column-major 128 x 128
+    // tile (float4 stores of 4 consecutive rows); the CTA that arrives last adds the segments'
+    // tiles in k order (the order of the shared tile core, so the same bits) with coalesced
+    // float4 loads, 16 per thread in flight, and applies the epilogue to what it summed.
+    static __device__ void fixup(const GemmParams<float> &p, Smem &sm, int t, int i, int j,
+                                 int slot, const float (&acc)[TM][TN], unsigned int epoch)
+    {
+        const int tid = threadIdx.x;
+        const int tx = tid % TX, ty = tid / TX;
         const int g = blockIdx.x;
         const int64_t S = p.sk_iters;
         const int G = p.grid;
@@ -566,10 +623,14 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         const int nseg = g1 - g0 + 1;
         float *mine = p.partial + (int64_t)(2 * g + slot) * (128 * 128);
 #pragma unroll
-        for (int ii = 0; ii < TM; ++ii)
+        for (int jj = 0; jj < TN; ++jj) {
+            const int col = ty * 4 + (jj % 4) + (jj / 4) * (128 / NCN);
 #pragma unroll
-            for (int jj = 0; jj < TN; ++jj)
-                __stcg(mine + (ii * TN + jj) * MATH_THREADS + tid, acc[ii][jj]);
+            for (int c = 0; c < NCM; ++c)
+                __stcg(reinterpret_cast<float4 *>(mine + col * 128 + tx * 4 + c * (128 / NCM)),
+                       make_float4(acc[c * 4 + 0][jj], acc[c * 4 + 1][jj], acc[c * 4 + 2][jj],
+                                   acc[c * 4 + 3][jj]));
+        }
         math_barrier();
         if (tid == 0) {
             __threadfence();
@@ -582,28 +643,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
             __threadfence();
         }
         math_barrier();
-        if (sm.flag) {
-            // the segments' partial sums added in k order, CHK values at a time (the
-            // accumulators already hold all the registers a thread can spare)
-            constexpr int NV = TM * TN, CHK = 16;
-            float *flat = &acc[0][0];
-#pragma unroll
-            for (int c0 = 0; c0 < NV; c0 += CHK) {
-                for (int gs = g0; gs <= g1; ++gs) {
-                    const int64_t lo = S * gs / G;
-                    const int gslot = (lo / p.kt == u) ? 0 : 1;
-                    const float *src = p.partial + (int64_t)(2 * gs + gslot) * (128 * 128);
-                    float v[CHK];
-#pragma unroll
-                    for (int e = 0; e < CHK; ++e)
-                        v[e] = __ldcg(src + (c0 + e) * MATH_THREADS + tid);
-#pragma unroll
-                    for (int e = 0; e < CHK; ++e)
-                        flat[c0 + e] = (gs == g0) ? v[e] : flat[c0 + e] + v[e];
-                }
-            }
-            epilogue(p, i, j, acc);
-        }
+        if (sm.flag) reduce_split_tile(p, i, j, u, g0, g1);
         math_barrier();
     }
 
