@@ -42,21 +42,30 @@ namespace gfip {
 namespace ws {
 
 // Math micro-tile: 16 x 8 per thread (4 chunks of 4 floats along m, 2 along n), so a
-// 128 x 128 tile takes 4 math warps.  Two CTAs of 4 + 2 warps fit an SM with 168 registers a
-// thread, which the 128 accumulators need (8 x 8 on 8 math warps would leave 96 and spill).
+// 128 x 128 tile takes one warpgroup of 4 math warps.  A CTA holds one SM: two math
+// warpgroups, each running the tiles of one "virtual CTA" of the shared schedule (ids
+// 2 * block and 2 * block + 1, so the grid, the split points and the bits are those of the
+// other FP32 kernels at two CTAs per SM), and one producer warpgroup (op(A) and op(B)
+// producers of each math warpgroup).  Registers: launched at 168 a thread (384 x 168 = 64512),
+// the producers drop to 56 and the math warpgroups rise to 224 (128 x 56 + 256 x 224 =
+// 64512), room for 128 accumulators and double-buffered fragments.
 struct Cfg {
     static constexpr int BM = 128, BN = 128, BK = 32, NCM = 4, NCN = 2;
     static constexpr int THREADS = BM * BN / (NCM * 4 * NCN * 4);
     static constexpr int UNROLL = 8;
-    static constexpr int STAGES = 3, MIN_BLOCKS = 2;
+    static constexpr int STAGES = 3, MIN_BLOCKS = 1;
 };
 static_assert(Cfg::BM == TileCfg<float>::BM && Cfg::BN == TileCfg<float>::BN &&
                   Cfg::BK == TileCfg<float>::BK,
               "the tile grid and its schedule are shared with the other FP32 kernels");
 
-constexpr int MATH_THREADS = Cfg::THREADS;     // 128
+constexpr int MATH_THREADS = Cfg::THREADS;     // 128: one warpgroup per virtual CTA
 constexpr int MATH_WARPS = MATH_THREADS / 32;  // 4
-constexpr int THREADS = MATH_THREADS + 64;     // + the A and B producer warps
+constexpr int VCTA = 2;                        // virtual CTAs (math warpgroups) per CTA
+constexpr int THREADS = (VCTA + 1) * 128;      // + the producer warpgroup
+constexpr int LAUNCH_REGS = 168, PRODUCER_REGS = 56, MATH_REGS = 224;
+static_assert(128 * PRODUCER_REGS + VCTA * 128 * MATH_REGS == THREADS * LAUNCH_REGS,
+              "the register split must add up to the launch's registers exactly");
 constexpr int STAGES = Cfg::STAGES;
 constexpr int TILE_FLOATS = 128 * 32;
 constexpr int TILE_BYTES = TILE_FLOATS * 4;    // one operand tile, packed or staged (16 KB)
@@ -70,12 +79,17 @@ __host__ __device__ constexpr int swz(int x, int kk)
     return (x >> 5) * 1024 + kk * 32 + ((((x & 31) >> 2) ^ (kk & 7)) << 2) + (x & 3);
 }
 
-struct __align__(128) Smem {
+// The stage ring of one math warpgroup.
+struct __align__(128) Ring {
     float a[STAGES][TILE_FLOATS];
     float b[STAGES][TILE_FLOATS];
     unsigned long long full[STAGES];
     unsigned long long empty[STAGES];
-    int flag;    // split-tile fix-up: this CTA adds the partial sums
+    int flag;    // split-tile fix-up: this virtual CTA adds the partial sums
+};
+
+struct __align__(128) Smem {
+    Ring ring[VCTA];
     int abort;   // a wait gave up: every role stops
 };
 
@@ -198,21 +212,14 @@ __device__ __forceinline__ void fence_proxy_shared()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ void math_barrier()
+// Named barrier of one math warpgroup (ids 1 and 2; 0 is __syncthreads).
+__device__ __forceinline__ void math_barrier(int ring)
 {
-    asm volatile("bar.sync 1, %0;" ::"n"(MATH_THREADS) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + ring), "n"(MATH_THREADS) : "memory");
 }
 
-// 16-byte shared-memory load at a 32-bit shared address plus a constant offset.
-template <int OFF> __device__ __forceinline__ void lds4(float *d, uint32_t addr)
-{
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
-                 : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-                 : "r"(addr), "n"(OFF));
-}
-
-// The segments one CTA runs, in order: whole tiles of the data-parallel waves, then its share
-// of the k-split tiles.  Every role walks the same sequence with its own cursor.
+// The segments one (virtual) CTA g runs, in order: whole tiles of the data-parallel waves,
+// then its share of the k-split tiles.  Every role walks the same sequence with its own cursor.
 struct Segment {
     int t, i, j, kb0, kb1;
     int slot;   // which of the CTA's two partial-sum slots a split segment uses
@@ -223,9 +230,8 @@ struct SegCursor {
     int64_t q, hi;      // next and end split iteration
     int first_u;
 
-    __device__ __forceinline__ void start(const GemmParams<float> &p)
+    __device__ __forceinline__ void start(const GemmParams<float> &p, int g)
     {
-        const int g = blockIdx.x;
         t = g;
         q = p.sk_iters * g / p.grid;
         hi = p.sk_iters * (g + 1) / p.grid;
@@ -340,8 +346,9 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
     };
 
     // ---- producer warps ------------------------------------------------------------------
-    // OPB: false = the op(A) producer (warp 4), true = the op(B) producer (warp 5).
-    template <bool OPB> static __device__ void producer(const GemmParams<float> &p, Smem &sm)
+    // OPB: false = the op(A) producer, true = the op(B) producer of ring r (virtual CTA g).
+    template <bool OPB>
+    static __device__ void producer(const GemmParams<float> &p, Smem &sm, Ring &rg, int g)
     {
         constexpr bool CONTIG = OPB ? BCONTIG : ACONTIG;
         const int lane = threadIdx.x & 31;
@@ -362,7 +369,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         bool ok = true;
 
         auto buf = [&](int st) -> uint32_t {
-            return smem_addr(OPB ? sm.b[st] : sm.a[st]);
+            return smem_addr(OPB ? rg.b[st] : rg.a[st]);
         };
         auto slot = [&](int panel, int kb) -> float * {
             return pack + ((int64_t)panel * p.kt + kb) * TILE_FLOATS;
@@ -373,7 +380,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
             const Meta &m = meta[d % STAGES];
             const int st = static_cast<int>(d % STAGES);
             if (m.prod) {
-                if (!mbar_wait(&sm.full[st], static_cast<uint32_t>((d / STAGES) & 1), sm,
+                if (!mbar_wait(&rg.full[st], static_cast<uint32_t>((d / STAGES) & 1), sm,
                                p.status)) {
                     ok = false;
                     return;
@@ -391,7 +398,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         };
 
         SegCursor cur;
-        cur.start(p);
+        cur.start(p, g);
         Segment sg;
         while (ok && !aborted(sm) && cur.next(p, sg)) {
             const int panel = OPB ? sg.j : sg.i;
@@ -409,7 +416,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
             for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
                 const int st = static_cast<int>(q % STAGES);
                 if (q >= STAGES &&
-                    !mbar_wait(&sm.empty[st], static_cast<uint32_t>(((q / STAGES) - 1) & 1), sm,
+                    !mbar_wait(&rg.empty[st], static_cast<uint32_t>(((q / STAGES) - 1) & 1), sm,
                                p.status)) {
                     ok = false;
                     break;
@@ -431,14 +438,14 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
                         }
                     }
                     // this lane's arrival, with the copy-engine bytes the stage waits for
-                    mbar_arrive_expect_tx(&sm.full[st], d == 1 ? TILE_BYTES : 0);
-                    if (d == 1) bulk_load(buf(st), slot(panel, kb), TILE_BYTES, &sm.full[st]);
+                    mbar_arrive_expect_tx(&rg.full[st], d == 1 ? TILE_BYTES : 0);
+                    if (d == 1) bulk_load(buf(st), slot(panel, kb), TILE_BYTES, &rg.full[st]);
                 }
                 d = __shfl_sync(0xffffffffu, d, 0);
                 if (d != 1)
                     raw_tile<CONTIG>(buf(st), X, ld, panel * 128, kb * 32, x_ext, p.k - kb * 32,
                                      lane);
-                cp_async_arrive(&sm.full[st]);
+                cp_async_arrive(&rg.full[st]);
                 Meta &m = meta[st];
                 m.prod = (d == 2);
                 m.panel = panel;
@@ -475,58 +482,86 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
             asm volatile("cp.async.wait_all;" ::: "memory");
             if (lane == 0)
                 for (long long d = q - 1; d >= 0 && d >= q - STAGES; --d)
-                    mbar_wait_drain(&sm.full[d % STAGES], static_cast<uint32_t>((d / STAGES) & 1));
+                    mbar_wait_drain(&rg.full[d % STAGES], static_cast<uint32_t>((d / STAGES) & 1));
         }
     }
 
     // ---- math warps ------------------------------------------------------------------------
-    // acc += A^T B over the 32 k rows of one stage.  Thread (tx, ty): A chunks c = 0..3 in
-    // segment c, chunk position tx; B chunks c = 0..1 in segment ty / 8 + 2 c, chunk position
-    // ty % 8.  In row kk the chunk position is XORed with kk % 8, which only touches address
-    // bits 4-6 (rows are 128 bytes, segments 4 KB): one XOR per operand per row.
-    // Row U (0..7) of an 8-row group whose row 0 is at ra / rb (chunk bits = tx, ty % 8).
+    // Fragments of one k row.  Thread (tx, ty): A chunks c = 0..3 in segment c at chunk
+    // position tx; B chunks c = 0..1 in segment ty / 8 + 2 c at chunk position ty % 8.  In row
+    // kk the chunk position is XORed with kk % 8, which only touches address bits 4-6 (rows
+    // are 128 bytes, segments 4 KB): the row's byte offset is (base ^ (U << 4)) + U * 128 for
+    // row U of an 8-row group whose row 0 sits at base.
     template <int U>
-    static __device__ __forceinline__ void krow(uint32_t ra, uint32_t rb, float (&acc)[TM][TN])
+    static __device__ __forceinline__ void load_row(const char *sa, const char *sb, uint32_t oa,
+                                                    uint32_t ob, float (&a)[TM], float (&b)[TN])
     {
-        const uint32_t xa = ra ^ (U << 4), xb = rb ^ (U << 4);
-        float a[TM], b[TN];
-        lds4<0 * 4096 + U * 128>(a + 0, xa);
-        lds4<1 * 4096 + U * 128>(a + 4, xa);
-        lds4<2 * 4096 + U * 128>(a + 8, xa);
-        lds4<3 * 4096 + U * 128>(a + 12, xa);
-        lds4<0 * 8192 + U * 128>(b + 0, xb);
-        lds4<1 * 8192 + U * 128>(b + 4, xb);
-        K::template fma_block<TM>(a, b, acc);
+        const char *pa = sa + ((oa ^ (U << 4)) + U * 128);
+        const char *pb = sb + ((ob ^ (U << 4)) + U * 128);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float4 v = *reinterpret_cast<const float4 *>(pa + c * 4096);
+            a[4 * c + 0] = v.x;
+            a[4 * c + 1] = v.y;
+            a[4 * c + 2] = v.z;
+            a[4 * c + 3] = v.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float4 v = *reinterpret_cast<const float4 *>(pb + c * 8192);
+            b[4 * c + 0] = v.x;
+            b[4 * c + 1] = v.y;
+            b[4 * c + 2] = v.z;
+            b[4 * c + 3] = v.w;
+        }
     }
 
-    static __device__ __forceinline__ void compute(uint32_t sa, uint32_t sb, float (&acc)[TM][TN],
-                                                   int tx, int ty)
+    // Row U of an 8-row group: the fragments of the next row are loaded first (double
+    // buffering), then row U's FFMA2 block.
+    template <int U>
+    static __device__ __forceinline__ void step(const char *sa, const char *sb, uint32_t oa,
+                                                uint32_t ob, bool more, float (&a)[2][TM],
+                                                float (&b)[2][TN], float (&acc)[TM][TN])
     {
-        uint32_t ra = sa + tx * 16;
-        uint32_t rb = sb + (ty >> 3) * 4096 + (ty & 7) * 16;
+        if constexpr (U < 7)
+            load_row<U + 1>(sa, sb, oa, ob, a[(U + 1) & 1], b[(U + 1) & 1]);
+        else if (more)
+            load_row<0>(sa, sb, oa + 8 * 128, ob + 8 * 128, a[0], b[0]);
+        K::template fma_block<TM>(a[U & 1], b[U & 1], acc);
+    }
+
+    // acc += A^T B over the 32 k rows of one stage.
+    static __device__ __forceinline__ void compute(const float *sa_, const float *sb_,
+                                                   float (&acc)[TM][TN], int tx, int ty)
+    {
+        const char *sa = reinterpret_cast<const char *>(sa_);
+        const char *sb = reinterpret_cast<const char *>(sb_);
+        uint32_t oa = tx * 16;
+        uint32_t ob = (ty >> 3) * 4096 + (ty & 7) * 16;
+        float a[2][TM], b[2][TN];
+        load_row<0>(sa, sb, oa, ob, a[0], b[0]);
 #pragma unroll 1
         for (int k0 = 0; k0 < 32; k0 += 8) {
-            krow<0>(ra, rb, acc);
-            krow<1>(ra, rb, acc);
-            krow<2>(ra, rb, acc);
-            krow<3>(ra, rb, acc);
-            krow<4>(ra, rb, acc);
-            krow<5>(ra, rb, acc);
-            krow<6>(ra, rb, acc);
-            krow<7>(ra, rb, acc);
-            ra += 8 * 128;
-            rb += 8 * 128;
+            const bool more = k0 + 8 < 32;
+            step<0>(sa, sb, oa, ob, more, a, b, acc);
+            step<1>(sa, sb, oa, ob, more, a, b, acc);
+            step<2>(sa, sb, oa, ob, more, a, b, acc);
+            step<3>(sa, sb, oa, ob, more, a, b, acc);
+            step<4>(sa, sb, oa, ob, more, a, b, acc);
+            step<5>(sa, sb, oa, ob, more, a, b, acc);
+            step<6>(sa, sb, oa, ob, more, a, b, acc);
+            step<7>(sa, sb, oa, ob, more, a, b, acc);
+            oa += 8 * 128;
+            ob += 8 * 128;
         }
     }
 
     // C[tile] := alpha*acc + beta*C[tile] (C not read when beta == 0), the operations of the
-    // shared tile core's epilogue, taking C four rows (one 16-byte chunk) at a time so that
-    // few registers are live beside the 128 accumulators.
-    static __device__ void epilogue(const GemmParams<float> &p, int i, int j,
+    // shared tile core's epilogue, taking C four rows (one 16-byte chunk) at a time.
+    static __device__ void epilogue(const GemmParams<float> &p, int i, int j, int tid,
                                     const float (&acc)[TM][TN])
     {
         constexpr int CH = 4;
-        const int tid = threadIdx.x;
         const int tx = tid % TX, ty = tid / TX;
         const bool read_c = (p.beta != 0.f);
 #pragma unroll
@@ -552,31 +587,30 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         }
     }
 
-    // The last CTA of a split tile: adds the segments' partial-sum tiles in k order and
-    // applies the epilogue.  Kept out of line: the accumulators are dead here, and the sums
-    // in flight get the registers to themselves.
-    static __device__ __noinline__ void reduce_split_tile(const GemmParams<float> &p, int i, int j,
-                                                          int u, int g0, int g1)
+    // The last virtual CTA of a split tile: adds the segments' partial-sum tiles in k order and
+    // applies the epilogue, with coalesced float4 loads, 8 per thread in flight (this thread's
+    // share: float4 f = tid + 128 r of the tile, r = 0..31, i.e. column f / 32, rows 4 (f % 32)).
+    static __device__ __forceinline__ void reduce_split_tile(const GemmParams<float> &p, int i,
+                                                             int j, int u, int g0, int g1,
+                                                             int tid)
     {
-        const int tid = threadIdx.x;
         const int64_t S = p.sk_iters;
         const int G = p.grid;
-        // float4 f = tid + 128 r (r = 0..31) of the tile: column f / 32, rows 4 (f % 32)
-        constexpr int HALF = 16;
+        constexpr int PART = 8;
         const bool read_c = (p.beta != 0.f);
 #pragma unroll 1
-        for (int r0 = 0; r0 < 32; r0 += HALF) {
-            float4 sum[HALF];
+        for (int r0 = 0; r0 < 32; r0 += PART) {
+            float4 sum[PART];
             for (int gs = g0; gs <= g1; ++gs) {
                 const int64_t lo = S * gs / G;
                 const int gslot = (lo / p.kt == u) ? 0 : 1;
                 const float4 *src = reinterpret_cast<const float4 *>(
                     p.partial + (int64_t)(2 * gs + gslot) * (128 * 128));
-                float4 v[HALF];
+                float4 v[PART];
 #pragma unroll
-                for (int r = 0; r < HALF; ++r) v[r] = __ldcg(src + tid + 128 * (r0 + r));
+                for (int r = 0; r < PART; ++r) v[r] = __ldcg(src + tid + 128 * (r0 + r));
 #pragma unroll
-                for (int r = 0; r < HALF; ++r) {
+                for (int r = 0; r < PART; ++r) {
                     if (gs == g0) {
                         sum[r] = v[r];
                     } else {
@@ -588,7 +622,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
                 }
             }
 #pragma unroll
-            for (int r = 0; r < HALF; ++r) {
+            for (int r = 0; r < PART; ++r) {
                 const int f = tid + 128 * (r0 + r);
                 const int col = j * 128 + f / 32, row0 = i * 128 + 4 * (f % 32);
                 if (col >= p.n) continue;
@@ -606,15 +640,13 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
     }
 
     // Split-tile fix-up.  Every segment stores its partial sums as a column-major 128 x 128
-    // tile (float4 stores of 4 consecutive rows); the CTA that arrives last adds the segments'
-    // tiles in k order (the order of the shared tile core, so the same bits) with coalesced
-    // float4 loads, 16 per thread in flight, and applies the epilogue to what it summed.
-    static __device__ void fixup(const GemmParams<float> &p, Smem &sm, int t, int i, int j,
-                                 int slot, const float (&acc)[TM][TN], unsigned int epoch)
+    // tile (float4 stores of 4 consecutive rows); the virtual CTA that arrives last adds the
+    // segments' tiles in k order (the order of the shared tile core, so the same bits).
+    static __device__ void fixup(const GemmParams<float> &p, Ring &rg, int ring, int g, int t,
+                                 int i, int j, int slot, const float (&acc)[TM][TN],
+                                 unsigned int epoch, int tid)
     {
-        const int tid = threadIdx.x;
         const int tx = tid % TX, ty = tid / TX;
-        const int g = blockIdx.x;
         const int64_t S = p.sk_iters;
         const int G = p.grid;
         const int u = t - p.dp_tiles;
@@ -631,7 +663,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
                        make_float4(acc[c * 4 + 0][jj], acc[c * 4 + 1][jj], acc[c * 4 + 2][jj],
                                    acc[c * 4 + 3][jj]));
         }
-        math_barrier();
+        math_barrier(ring);
         if (tid == 0) {
             __threadfence();
             const unsigned long long tag = static_cast<unsigned long long>(epoch) << 32;
@@ -639,17 +671,17 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
             const unsigned long long old = atomicAdd(p.tile_count + t, 1ull);
             const long long cnt = static_cast<long long>(old - tag) + 1;
             if ((old >> 32) != epoch || cnt > nseg) atomicOr(p.status, STATUS_BAD_SEGMENT);
-            sm.flag = (cnt == nseg);
+            rg.flag = (cnt == nseg);
             __threadfence();
         }
-        math_barrier();
-        if (sm.flag) reduce_split_tile(p, i, j, u, g0, g1);
-        math_barrier();
+        math_barrier(ring);
+        if (rg.flag) reduce_split_tile(p, i, j, u, g0, g1, tid);
+        math_barrier(ring);
     }
 
-    static __device__ void math(const GemmParams<float> &p, Smem &sm)
+    static __device__ void math(const GemmParams<float> &p, Smem &sm, Ring &rg, int ring, int g)
     {
-        const int tid = threadIdx.x;
+        const int tid = threadIdx.x & (MATH_THREADS - 1);
         const int tx = tid % TX, ty = tid / TX;
         unsigned int epoch = 0u;
         if (tid == 0) epoch = *(volatile unsigned int *)p.launch_count + 1u;
@@ -657,7 +689,7 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         int st = 0;          // stage of the next k-block
         uint32_t ph = 0;     // parity of that stage's next full phase
         SegCursor cur;
-        cur.start(p);
+        cur.start(p, g);
         Segment sg;
         bool ok = true;
         while (ok && cur.next(p, sg)) {
@@ -677,13 +709,13 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
                 }
             }
             for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
-                if (!mbar_wait(&sm.full[st], ph, sm, p.status)) {
+                if (!mbar_wait(&rg.full[st], ph, sm, p.status)) {
                     ok = false;
                     break;
                 }
-                compute(smem_addr(sm.a[st]), smem_addr(sm.b[st]), acc, tx, ty);
+                compute(rg.a[st], rg.b[st], acc, tx, ty);
                 __syncwarp();
-                if ((tid & 31) == 0) mbar_arrive(&sm.empty[st]);
+                if ((tid & 31) == 0) mbar_arrive(&rg.empty[st]);
                 if (++st == STAGES) {
                     st = 0;
                     ph ^= 1u;
@@ -691,36 +723,51 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
             }
             if (!ok) break;
             if (sg.kb0 == 0 && sg.kb1 == p.kt)
-                epilogue(p, i, j, acc);
+                epilogue(p, i, j, tid, acc);
             else
-                fixup(p, sm, sg.t, i, j, sg.slot, acc, epoch);
+                fixup(p, rg, ring, g, sg.t, i, j, sg.slot, acc, epoch, tid);
         }
     }
 };
 
-// The launch's epoch tags its ready words and arrival counters exactly as in gemm_kernel:
-// every role reads the launch counter at start, and the last CTA to finish advances it.
+// One CTA per SM: warpgroups 0 and 1 are the math warpgroups of virtual CTAs 2 * block and
+// 2 * block + 1 (a virtual id at or past the grid has no work), warpgroup 2 holds their
+// producers (warp 8 + 2 r: op(A) of ring r, warp 9 + 2 r: op(B)).  The launch's epoch tags its
+// ready words and arrival counters exactly as in gemm_kernel: every role reads the launch
+// counter at start, and the last CTA to finish advances it.
 template <bool ACONTIG, bool BCONTIG>
-__global__ void __launch_bounds__(THREADS, 2) ws_gemm_kernel(const GemmParams<float> p)
+__global__ void __launch_bounds__(THREADS, 1) ws_gemm_kernel(const GemmParams<float> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int warp = threadIdx.x >> 5;
+    const int wg = warp >> 2;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&sm.full[s], 2 * 33);   // per producer: 32 lanes' copies + expect_tx
-            mbar_init(&sm.empty[s], MATH_WARPS);
-        }
+        for (int r = 0; r < VCTA; ++r)
+            for (int s = 0; s < STAGES; ++s) {
+                mbar_init(&sm.ring[r].full[s], 2 * 33);   // A and B producers: 32 lanes + tx
+                mbar_init(&sm.ring[r].empty[s], MATH_WARPS);
+            }
         sm.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (warp == MATH_WARPS)
-        WsKernel<ACONTIG, BCONTIG>::template producer<false>(p, sm);
-    else if (warp == MATH_WARPS + 1)
-        WsKernel<ACONTIG, BCONTIG>::template producer<true>(p, sm);
-    else
-        WsKernel<ACONTIG, BCONTIG>::math(p, sm);
+    if (wg == VCTA) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(PRODUCER_REGS));
+        const int w = warp - 4 * VCTA;          // 0..3
+        const int r = w >> 1;
+        const int g = VCTA * blockIdx.x + r;
+        if (g < p.grid) {
+            if (w & 1)
+                WsKernel<ACONTIG, BCONTIG>::template producer<true>(p, sm, sm.ring[r], g);
+            else
+                WsKernel<ACONTIG, BCONTIG>::template producer<false>(p, sm, sm.ring[r], g);
+        }
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(MATH_REGS));
+        const int g = VCTA * blockIdx.x + wg;
+        if (g < p.grid) WsKernel<ACONTIG, BCONTIG>::math(p, sm, sm.ring[wg], wg, g);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -776,13 +823,20 @@ inline size_t smem_bytes()
 
 constexpr size_t PACK_SMEM = (size_t)PACK_WARPS * TILE_BYTES;
 
+// The register split of the warpgroups (setmaxnreg) assumes the kernel is launched with
+// exactly LAUNCH_REGS registers a thread: with fewer, the math warpgroups' increase could never
+// be granted.  A build where the compiler chose another count is refused here.
 template <bool AC, bool BC> cudaError_t configure()
 {
     static bool configured = false;
     if (configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(ws_gemm_kernel<AC, BC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem_bytes()));
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, ws_gemm_kernel<AC, BC>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != LAUNCH_REGS) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(ws_gemm_kernel<AC, BC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem_bytes()));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ws_pack_kernel<AC, BC>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -795,7 +849,7 @@ template <bool AC, bool BC> cudaError_t launch_t(const GemmParams<float> &p, cud
 {
     cudaError_t e = configure<AC, BC>();
     if (e != cudaSuccess) return e;
-    ws_gemm_kernel<AC, BC><<<p.grid, THREADS, smem_bytes(), s>>>(p);
+    ws_gemm_kernel<AC, BC><<<(p.grid + VCTA - 1) / VCTA, THREADS, smem_bytes(), s>>>(p);
     return cudaGetLastError();
 }
 
@@ -810,6 +864,7 @@ template <bool AC, bool BC> cudaError_t launch_pack_t(const PackParams<float> &p
     return cudaGetLastError();
 }
 
+// Virtual CTAs per SM (the unit of the shared schedule): VCTA per resident CTA.
 template <bool AC, bool BC> int blocks_per_sm_one()
 {
     if (configure<AC, BC>() != cudaSuccess) return 0;
@@ -817,7 +872,7 @@ template <bool AC, bool BC> int blocks_per_sm_one()
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ws_gemm_kernel<AC, BC>, THREADS,
                                                       smem_bytes()) != cudaSuccess)
         return 0;
-    return n;
+    return n * VCTA;
 }
 
 }  // namespace ws
