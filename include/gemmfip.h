@@ -13,11 +13,11 @@
  * contiguous tile layout the first time a CTA computes with it, in the same pass ("fused-in
  * packing"); later CTAs load the packed copy.  Which operands are worth packing follows the
  * option table of Sec. 3.3 (pack A only if the result has more than one tile column, pack
- * B only if it has more than one tile row), and packing is used only when some tiles run
- * after the first wave of CTAs, since only those can read a finished packed copy.  The two comparison variants of Sec. 2.3-2.4
- * are exported as well: a direct-strided kernel that never packs (the SUP path) and a
- * pack-then-compute pair of launches (the conventional path).  All three produce
- * bit-identical results for the same arguments on the same GPU.
+ * B only if it has more than one tile row); one scheme serves every size, and a tile reads a
+ * k-block packed whenever its producer has already published it.  The two comparison
+ * variants of Sec. 2.3-2.4 are exported as well: a direct-strided kernel that never packs (the
+ * SUP path) and a pack-then-compute pair of launches (the conventional path).  All three
+ * produce bit-identical results for the same arguments on the same GPU.
  *
  * Pointers: A, B and C are DEVICE pointers owned by the caller; A and B are only read;
  * only the m x n logical region of C is written (rows m..ldc-1 are never touched).  Calls
@@ -78,16 +78,15 @@ typedef struct gfip_handle_s *gfip_handle_t;
 
 /* Pack policies for gfip_set_pack_policy(). */
 #define GFIP_PACK_AUTO 0        /* Sec. 3.3 option table: pack A iff > 1 tile column, B iff > 1 tile
-                                   row; with line producers (GFIP_PACKER_LINE) only when some
-                                   tiles run after the first wave of CTAs                           */
+                                   row (whether a tile finds a k-block already packed is decided
+                                   at run time, per k-block)                                        */
 #define GFIP_PACK_NONE 1        /* never pack (the fused kernel then equals the direct variant)          */
 #define GFIP_PACK_A 2           /* pack A panels only                                                   */
 #define GFIP_PACK_B 3           /* pack B panels only                                                   */
 #define GFIP_PACK_BOTH 4        /* pack both operands regardless of reuse                               */
 
 /* Packers for gfip_set_packer(): which CTAs write the packed copies in the fused routines. */
-#define GFIP_PACKER_AUTO 0      /* SHARED for FP32 GEMMs with at least 16 k-blocks of work per
-                                   CTA (tiles x k-blocks >= 16 x CTAs), else LINE                */
+#define GFIP_PACKER_AUTO 0      /* LINE, at every size                                       */
 #define GFIP_PACKER_LINE 1      /* the first tile column packs A, the first tile row B, while
                                    computing their own tiles (Alg. 1, Sec. 3.2)                   */
 #define GFIP_PACKER_SHARED 2    /* every CTA first packs an equal share of all packed tiles,

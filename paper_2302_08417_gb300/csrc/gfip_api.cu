@@ -27,7 +27,9 @@ constexpr size_t kPackCountOffset = 192;    // header word: tiles packed by shar
 constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
 constexpr int kMinSplitRun = 8;              // shortest k run per CTA in a split wave
 constexpr int kTrsmPanel = 512;              // TRSM: unknowns per panel (two-level blocking)
-constexpr int kSharedMinRun = 16;            // AUTO packer: shared from this many k-blocks per CTA
+// Split tiles of an FP32 launch with fewer tiles than CTAs: each CTA takes at least this many
+// k-blocks, so a 128 x 128 tile is summed from a few partial tiles, not from one per k-block.
+constexpr int kMinSplitRunF32 = 4;
 constexpr unsigned long long kOzakiWaitNs = 2000000000ull;  // 2 s per pipeline wait
 
 struct Handle {
@@ -111,18 +113,6 @@ template <typename T> int blocks_per_sm(Handle *h)
     return slot;
 }
 
-// Who packs when the packer is AUTO: all CTAs up front (shared) for FP32 GEMMs that give each
-// CTA at least kSharedMinRun k-blocks of work, where the FFMA loop pays for every
-// element-wise raw load a tile makes and the short pre-pass before the tiles costs less
-// (measured: +1.2 % to +4.3 % over line producers from 1536^3 to 8192^3, -1 % to -5 % at
-// 768^3 and 1024^3 with 3 and 7 k-blocks per CTA); the first tile line (Alg. 1) for FP64,
-// whose DFMA-bound loop hides the raw loads (both packers measured equal at 8192^3), and
-// for short runs, where the pre-pass would not be repaid.
-template <typename T> bool auto_shared(const Plan<T> &pl)
-{
-    return sizeof(T) == 4 && (int64_t)pl.tiles * pl.kt >= (int64_t)kSharedMinRun * pl.grid;
-}
-
 template <typename T>
 Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI_NONE,
                   bool masked = false)
@@ -147,7 +137,9 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI
         pl.dp_tiles = pl.tiles;
         pl.sk_iters = 0;
     } else if (pl.tiles < full) {
-        pl.grid = static_cast<int>(std::min<int64_t>(full, total_iters));
+        const int64_t run = sizeof(T) == 4 ? kMinSplitRunF32 : 1;
+        pl.grid = static_cast<int>(std::min<int64_t>(full, std::max<int64_t>(
+                                                               pl.tiles, (total_iters + run - 1) / run)));
         pl.dp_tiles = 0;
         pl.sk_iters = total_iters;
     } else {
@@ -162,11 +154,11 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI
         pl.sk_iters = (int64_t)sk_tiles * pl.kt;
     }
 
-    // Who packs: shared packing only for whole rectangles of dense operands (a triangle's
-    // panels are shared by both roles, and masked blocks are never packed whole).
+    // Who packs: the first tile line (Alg. 1) at every size; the collaborative pre-pass only on
+    // request, and only for whole rectangles of dense operands (a triangle's panels are shared
+    // by both roles, and masked blocks are never packed whole).
     if (v == Variant::Fused && tri == gfip::TRI_NONE && !masked)
-        pl.shared = h->packer == GFIP_PACKER_SHARED ||
-                    (h->packer == GFIP_PACKER_AUTO && auto_shared<T>(pl));
+        pl.shared = h->packer == GFIP_PACKER_SHARED;
 
     // Which operands are packed, and how (Sec. 3.3 option table for the fused variant).
     switch (v) {
@@ -192,18 +184,14 @@ Plan<T> make_plan(Handle *h, Variant v, int m, int n, int k, int tri = gfip::TRI
         case GFIP_PACK_BOTH:
             pl.mode_a = pl.mode_b = gfip::MODE_FIP;
             break;
-        default: {
-            // AUTO: Sec. 3.3's table (an A panel is reused only across tile columns, a B
-            // panel only across tile rows), read for a GPU.  With line producers a packed
-            // copy pays off only for tiles that run after its producer, i.e. when a whole
-            // data-parallel wave (which holds the producers) runs before other tiles; tiles
-            // running side by side with the producer read the raw operand.  Shared packing
-            // publishes every panel before the tiles start, so reuse alone decides.
-            const bool later = pl.shared || (pl.tiles > pl.grid && pl.dp_tiles >= pl.grid);
-            pl.mode_a = (pl.nt > 1 && later) ? gfip::MODE_FIP : gfip::MODE_RAW;
-            pl.mode_b = (pl.mt > 1 && later) ? gfip::MODE_FIP : gfip::MODE_RAW;
+        default:
+            // AUTO: Sec. 3.3's table: an A panel is reused only across tile columns, a B
+            // panel only across tile rows, so pack A iff there is more than one tile column
+            // and B iff there is more than one tile row.  Whether a consumer finds a k-block
+            // already published is decided at run time, per k-block (Sec. 3.2's cases).
+            pl.mode_a = (pl.nt > 1) ? gfip::MODE_FIP : gfip::MODE_RAW;
+            pl.mode_b = (pl.mt > 1) ? gfip::MODE_FIP : gfip::MODE_RAW;
             break;
-        }
         }
         break;
     }
