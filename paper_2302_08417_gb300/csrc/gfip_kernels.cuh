@@ -362,6 +362,45 @@ template <typename P> __device__ __forceinline__ void tile_of(const P &p, int t,
         tile_coords(t, p.mt, p.nt, p.band, i, j);
 }
 
+// Position of tile (i, j) in the launch's tile order of a whole C (inverse of tile_coords).
+__device__ __forceinline__ int tile_index(int i, int j, int mt, int nt, int band)
+{
+    if (j == 0) return i;
+    if (i == 0) return mt + j - 1;
+    const int rows = mt - 1, cols = nt - 1;
+    const int b = (i - 1) / band;
+    const int h = min(band, rows - b * band);
+    return mt + nt - 1 + b * band * cols + (j - 1) * h + (i - 1 - b * band);
+}
+
+// Round in which tile t starts: its data-parallel wave, or, for the k-split tiles, the round
+// after the data-parallel waves (their segments run side by side).
+template <typename P> __device__ __forceinline__ int tile_round(const P &p, int t)
+{
+    return min(t, p.dp_tiles) / p.grid;
+}
+
+// The run-time reuse logic of the unified method (Sec. 3.3's table, which the paper's
+// conclusion has a runtime logic apply per micropanel), read in time for a GPU: a packed copy
+// of a panel is only ever read by tiles that start after its producer has published it, so a
+// panel is worth packing iff its last consumer tile starts in a later round than its producer
+// (A panel i: producer (i, 0), consumers (i, j >= 1); B panel j: producer (0, j), consumers
+// (i >= 1, j)).  Tiles of one round run side by side and read the raw operand.  Small problems
+// (one round) thus pack nothing, large ones every panel, and the code path is the same.  A
+// triangle (SYRK) and shared packing pack every panel the table allows.
+template <typename P> __device__ __forceinline__ bool reused_a(const P &p, int i)
+{
+    if (p.tri != TRI_NONE || p.shared_pack) return true;
+    return p.nt > 1 && tile_round(p, tile_index(i, p.nt - 1, p.mt, p.nt, p.band)) >
+                           tile_round(p, tile_index(i, 0, p.mt, p.nt, p.band));
+}
+template <typename P> __device__ __forceinline__ bool reused_b(const P &p, int j)
+{
+    if (p.tri != TRI_NONE || p.shared_pack) return true;
+    return p.mt > 1 && tile_round(p, tile_index(p.mt - 1, j, p.mt, p.nt, p.band)) >
+                           tile_round(p, tile_index(0, j, p.mt, p.nt, p.band));
+}
+
 template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     using Cfg = C;
     T a[Cfg::STAGES][TileLayout<T, Cfg::BM, Cfg::BK>::ELEMS];
@@ -370,6 +409,7 @@ template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     int dec_b[2 * Cfg::STAGES];
     int part[2 * Cfg::STAGES];   // bit 0 (1): the A (B) block is cut by a triangular mask
     int full_a, full_b;  // the tile's whole A (B) panel is already published
+    int mode_a, mode_b;  // the segment's operand modes after the reuse logic (reused_a/_b)
     int watch;           // shared packing: the count of packed tiles is not complete yet
     int flag;
 };
@@ -459,9 +499,9 @@ struct Kernel {
                                                         int kb)
     {
         Words w{0ull, 0ull};
-        if (need_word(p.mode_a, prod_a(p, j), sm.full_a))
+        if (need_word(sm.mode_a, prod_a(p, j), sm.full_a))
             w.a = ld_relaxed(p.state_a + (int64_t)i * p.kt + kb);
-        if (need_word(p.mode_b, prod_b(p, i), sm.full_b))
+        if (need_word(sm.mode_b, prod_b(p, i), sm.full_b))
             w.b = ld_relaxed(p.state_b + (int64_t)j * p.kt + kb);
         return w;
     }
@@ -472,8 +512,8 @@ struct Kernel {
                                                            Smem &sm, int i, int j, int kb,
                                                            Words w, int q, unsigned int epoch)
     {
-        int da = classify(p.mode_a, prod_a(p, j), sm.full_a, w.a, epoch);
-        int db = classify(p.mode_b, prod_b(p, i), sm.full_b, w.b, epoch);
+        int da = classify(sm.mode_a, prod_a(p, j), sm.full_a, w.a, epoch);
+        int db = classify(sm.mode_b, prod_b(p, i), sm.full_b, w.b, epoch);
         if constexpr (TMASK) {
             // triangular operands: a k-block in which either operand block lies outside its
             // triangle contributes nothing and is not computed; an operand block is then not
@@ -491,8 +531,8 @@ struct Kernel {
         }
         sm.dec_a[q % DEC] = da;
         sm.dec_b[q % DEC] = db;
-        return (da == DEC_PACKED && p.mode_a == MODE_FIP && !sm.full_a) ||
-               (db == DEC_PACKED && p.mode_b == MODE_FIP && !sm.full_b);
+        return (da == DEC_PACKED && sm.mode_a == MODE_FIP && !sm.full_a) ||
+               (db == DEC_PACKED && sm.mode_b == MODE_FIP && !sm.full_b);
     }
 
     static __device__ __forceinline__ void issue(const GemmParams<T> &p, Smem &sm,
@@ -684,13 +724,16 @@ struct Kernel {
             // a panel whose producer finished it whole needs no per-k-block look-ups; with
             // shared packing, every panel is whole once all CTAs have counted their tiles
             // (until then thread 0 watches the count, loaded in place of the words)
+            // operands of panels that no later tile reuses are read raw here (reused_a/_b)
+            sm.mode_a = (p.mode_a == MODE_FIP && !reused_a(p, i)) ? MODE_RAW : p.mode_a;
+            sm.mode_b = (p.mode_b == MODE_FIP && !reused_b(p, j)) ? MODE_RAW : p.mode_b;
             const bool all = !TMASK && p.shared_pack &&
                              ld_relaxed(p.pack_count) == all_packed(p, epoch);
             sm.watch = !TMASK && p.shared_pack && !all;
-            const bool fa = need_word(p.mode_a, prod_a(p, j), 0) &&
+            const bool fa = need_word(sm.mode_a, prod_a(p, j), 0) &&
                             (all || ld_relaxed(p.state_a + (int64_t)p.mt * p.kt + i) ==
                                         ready_value(epoch));
-            const bool fb = need_word(p.mode_b, prod_b(p, i), 0) &&
+            const bool fb = need_word(sm.mode_b, prod_b(p, i), 0) &&
                             (all || ld_relaxed(p.state_b + (int64_t)p.nt * p.kt + j) ==
                                         ready_value(epoch));
             sm.full_a = fa;
@@ -747,8 +790,8 @@ struct Kernel {
                 if (!TMASK && ahead && p.shared_pack && sm.watch &&
                     w.a == all_packed(p, epoch)) {
                     // every panel is packed: k-blocks from it + STAGES on read the copies
-                    sm.full_a = need_word(p.mode_a, false, 0);
-                    sm.full_b = need_word(p.mode_b, false, 0);
+                    sm.full_a = need_word(sm.mode_a, false, 0);
+                    sm.full_b = need_word(sm.mode_b, false, 0);
                     sm.watch = 0;
                     fence_acquire();
                 }
@@ -765,9 +808,9 @@ struct Kernel {
             publish_produced(p, sm, i, j, kb0, nkb - 1, epoch);
             // a producer that covered its whole panel publishes the panel as complete
             if (kb0 == 0 && kb1 == p.kt) {
-                if (p.mode_a == MODE_FIP && prod_a(p, j))
+                if (sm.mode_a == MODE_FIP && prod_a(p, j))
                     publish(p.state_a + (int64_t)p.mt * p.kt + i, epoch);
-                if (p.mode_b == MODE_FIP && prod_b(p, i))
+                if (sm.mode_b == MODE_FIP && prod_b(p, i))
                     publish(p.state_b + (int64_t)p.nt * p.kt + j, epoch);
             }
         }

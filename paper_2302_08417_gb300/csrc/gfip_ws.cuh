@@ -403,10 +403,14 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         while (ok && !aborted(sm) && cur.next(p, sg)) {
             const int panel = OPB ? sg.j : sg.i;
             const int other = OPB ? sg.i : sg.j;
-            const bool prod = mode == MODE_FIP && other == 0 && produces;
+            // a panel that no later tile reuses is neither packed nor looked up (reused_a/_b)
+            const int emode =
+                (mode == MODE_FIP && !(OPB ? reused_b(p, panel) : reused_a(p, panel))) ? MODE_RAW
+                                                                                        : mode;
+            const bool prod = emode == MODE_FIP && other == 0 && produces;
             // a panel its producer finished whole needs no per-k-block look-ups
             bool full = false;
-            if (lane == 0 && mode == MODE_FIP && !prod) {
+            if (lane == 0 && emode == MODE_FIP && !prod) {
                 full = ld_relaxed(state + (int64_t)npanels * p.kt + panel) == ready;
                 if (full) {
                     fence_acquire();
@@ -424,9 +428,9 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
                 // decision (Sec. 3.2's cases, for this operand): 0 raw, 1 packed, 2 produce
                 int d = 0;
                 if (lane == 0) {
-                    if (mode == MODE_PACKED) {
+                    if (emode == MODE_PACKED) {
                         d = 1;
-                    } else if (mode == MODE_FIP) {
+                    } else if (emode == MODE_FIP) {
                         if (prod) {
                             d = 2;
                         } else if (full) {
