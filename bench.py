@@ -8,7 +8,8 @@ headline workload (m = n = k = 8192, transa = transb = 'N', lda = ldb = ldc = 81
 Prints ONE JSON line: GFLOP/s over the timed steps (device time, CUDA events), the roofline
 of the dominant kernel against the FP64 DFMA rate, the end-to-end figure through the public
 API with host buffers, the oracle timed on the host cores on a bounded sample, the SM clocks
-seen during the timed region, and a compact fused-vs-plain size spectrum.
+seen during the timed region, the fused-vs-plain spectrum over all 20 sizes in both dtypes
+(with per-size noise bands), and, last, a compact summary of all of it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-spectrum]
 
@@ -217,53 +218,117 @@ def cpu_oracle_sample(A_host, B_host, C_host, m, k, lda, ldb, ldc, budget_s=12.0
                       f"{dt:.1f} s, FP64 j-p-i triple loop, OpenMP over columns"}
 
 
-def spectrum(h, g, torch, sizes=(16, 64, 256, 1024, 4096), reps=5):
-    """Fused vs direct vs pack-then-compute GFLOP/s, N/N, ld = m + 7, beta = 0.5."""
-    out = {}
-    for dtype, esz, tag in ((torch.float64, 8, "f64"), (torch.float32, 4, "f32")):
-        rows = {}
-        for n in sizes:
-            A, B, C = make_operands(n, dtype, n, n, n)
-            ld = n + PAD
-            h.ensure_workspace("N", "N", n, n, n, esz)
-            row = {}
-            for var in ("fused", "direct", "pack_then_compute"):
-                name = g.ENTRY[(var, esz)]
-
-                def call():
-                    rc = g._gemm_call(name, h.h, "N", "N", n, n, n, ALPHA, A.data_ptr(), ld,
-                                      B.data_ptr(), ld, BETA, C.data_ptr(), ld)
-                    assert rc == 0, rc
-                for _ in range(2):
-                    call()
-                torch.cuda.synchronize()
-                best = float("inf")
-                r = reps if n <= 1024 else 2
-                for _ in range(r):
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record()
-                    call()
-                    e1.record()
-                    e1.synchronize()
-                    best = min(best, e0.elapsed_time(e1))
-                row[var] = round(gflop(n, n, n) / (best * 1e-3), 1)
-            rows[str(n)] = row
-        out[tag] = rows
+def oracle_single_thread(sizes=(256, 512, 1024, 2048)):
+    """The oracle on ONE host core (the paper's single-core framing) for m = n = k <= 2048,
+    N/N, ld = m + 7, alpha 1, beta 0.5, uniform[-1, 1]; the headline size is extrapolated
+    from the largest one as n^3 and labelled so."""
+    import numpy as np
+    import oracle
+    from paper_2302_08417_gb300 import inputs
+    oracle.build()
+    out = {"note": "one thread, FP64 j-p-i triple loop; seconds per call and GFLOP/s"}
+    last = None
+    for n in sizes:
+        p = inputs.problem(n, "N", "N", n, n, n, ALPHA, BETA, PAD, PAD, PAD)
+        C = p.C0.copy()
+        t0 = time.perf_counter()
+        rc = oracle.gemm("N", "N", n, n, n, ALPHA, p.A, p.lda, p.B, p.ldb, BETA, C, p.ldc,
+                         nthreads=1)
+        dt = time.perf_counter() - t0
+        assert rc == 0
+        out[str(n)] = {"s": round(dt, 4), "gflops": round(gflop(n, n, n) / dt, 3)}
+        last = (n, dt)
+    n0, t0_ = last
+    out["8192_extrapolated_s"] = round(t0_ * (8192 / n0) ** 3, 1)
+    out["8192_extrapolated_note"] = f"extrapolated as n^3 from {n0}, not measured"
     return out
 
 
-def sweep(h, g, torch, sizes, dtypes=("f64", "f32"), target_ms=2.0):
-    """The fused-vs-plain size spectrum, N/N, ld = m + 7, alpha 1, beta 0.5, uniform[-1, 1].
+VARIANTS = ("fused", "direct", "pack_then_compute")
 
-    For every size, dtype and variant two times per call are taken: `dev_us`, the device time
-    of R back-to-back calls captured in one CUDA graph (replayed, best of 3, divided by R), and
-    `call_us`, R eager calls from Python between two events (host overhead included).  R is 1
-    when one call takes more than half a millisecond.  Operands of the sizes below about 2048
-    stay in L2 between calls (warm), as they would in a loop of calls."""
-    import math
-    out = {"note": "N/N, ld = m + 7, alpha 1, beta 0.5, uniform[-1,1]; dev_us from CUDA-graph "
-                   "replays of R calls, call_us from R eager calls; GFLOP/s from dev_us"}
+
+class VariantTimer:
+    """Device time per call of one GEMM call shape in each variant.  Calls shorter than half a
+    millisecond are captured R at a time (R calls >= target_ms) in one CUDA graph per variant
+    and replayed; longer ones are timed as single calls.  Each timing is one replay (or call)
+    between two CUDA events on the launching stream."""
+
+    def __init__(self, h, g, torch, esz, ta, tb, m, n, k, A, lda, B, ldb, beta, C, ldc,
+                 target_ms=2.0):
+        import math
+        self.torch, self.h = torch, h
+        self.fns, self.reps = {}, {}
+        for var in VARIANTS:
+            name = g.ENTRY[(var, esz)]
+
+            def call(name=name):
+                rc = g._gemm_call(name, h.h, ta, tb, m, n, k, ALPHA, A.data_ptr(), lda,
+                                  B.data_ptr(), ldb, beta, C.data_ptr(), ldc)
+                if rc != 0:
+                    raise g.GemmError(rc, name)
+            one = self._events_ms(call)     # the first call also warms up
+            if one > 0.5:
+                self.fns[var], self.reps[var] = call, 1
+                continue
+            R = max(1, min(400, math.ceil(target_ms / max(one, 1e-3))))
+
+            def burst(call=call, R=R):
+                for _ in range(R):
+                    call()
+            stream = torch.cuda.Stream()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(stream):
+                h.bind_stream(stream)
+                with torch.cuda.graph(graph, stream=stream):
+                    burst()
+            h.bind_stream()
+            graph.replay()
+            torch.cuda.synchronize()
+            self.fns[var], self.reps[var] = graph.replay, R
+            setattr(self, f"_graph_{var}", graph)
+
+    def _events_ms(self, fn):
+        torch = self.torch
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def run(self, rounds):
+        """Per variant: the device times per call of `rounds` timings, taken round-robin over
+        the variants so that clock or thermal drift touches all of them alike."""
+        out = {v: [] for v in VARIANTS}
+        for _ in range(rounds):
+            for v in VARIANTS:
+                out[v].append(self._events_ms(self.fns[v]) / self.reps[v])
+        return out
+
+
+def summarize(times, flop, peak):
+    """Median GFLOP/s per variant, fused / best plain variant, and the noise band: the largest
+    relative spread (max - min) / median of the timings of any variant."""
+    med = {v: statistics.median(t) for v, t in times.items()}
+    gf = {v: flop / 1e9 / (med[v] * 1e-3) for v in med}
+    noise = max((max(t) - min(t)) / statistics.median(t) for t in times.values())
+    best_plain = max(gf["direct"], gf["pack_then_compute"])
+    return {"gflops": {v: round(gf[v], 2) for v in VARIANTS},
+            "dev_us": {v: round(med[v] * 1e3, 2) for v in VARIANTS},
+            "fused_over_best_plain": round(gf["fused"] / best_plain, 4),
+            "noise": round(noise, 4), "frac": round(gf["fused"] / peak, 4)}
+
+
+def sweep(h, g, torch, sizes, dtypes=("f64", "f32"), rounds=7, long_rounds=3):
+    """The fused-vs-plain size spectrum, N/N, ld = m + 7, alpha 1, beta 0.5, uniform[-1, 1]:
+    every size of the 16..16384 spectrum in FP64 and FP32, the three variants timed
+    round-robin (`rounds` rounds, `long_rounds` when one call takes over 100 ms).  Operands of
+    the sizes below about 2048 stay in L2 between calls (warm), as they would in a loop of
+    calls."""
+    out = {"note": "N/N, ld = m + 7, alpha 1, beta 0.5, uniform[-1,1]; median device time "
+                   "per call over rounds of graph-replayed calls; noise = largest (max-min)/"
+                   "median of a variant's timings"}
     for tag in dtypes:
         dtype = torch.float64 if tag == "f64" else torch.float32
         esz = 8 if tag == "f64" else 4
@@ -273,64 +338,51 @@ def sweep(h, g, torch, sizes, dtypes=("f64", "f32"), target_ms=2.0):
             A, B, C = make_operands(n, dtype, n, n, n)
             ld = n + PAD
             h.ensure_workspace("N", "N", n, n, n, esz)
-            row = {}
-            for var in ("fused", "direct", "pack_then_compute"):
-                name = g.ENTRY[(var, esz)]
-
-                def call():
-                    rc = g._gemm_call(name, h.h, "N", "N", n, n, n, ALPHA, A.data_ptr(), ld,
-                                      B.data_ptr(), ld, BETA, C.data_ptr(), ld)
-                    if rc != 0:
-                        raise g.GemmError(rc, name)
-
-                def events_ms(fn, reps):
-                    best = float("inf")
-                    for _ in range(reps):
-                        e0 = torch.cuda.Event(enable_timing=True)
-                        e1 = torch.cuda.Event(enable_timing=True)
-                        e0.record()
-                        fn()
-                        e1.record()
-                        e1.synchronize()
-                        best = min(best, e0.elapsed_time(e1))
-                    return best
-                call()
-                torch.cuda.synchronize()
-                one = events_ms(call, 1)
-                if one > 0.5:
-                    extra = 0 if one > 2000 else (1 if one > 500 else 2)
-                    dev = min(one, events_ms(call, extra)) if extra else one
-                    reps_per, call_ms, dev_ms = 1, dev, dev
-                else:
-                    R = max(1, min(400, math.ceil(target_ms / max(one, 1e-3))))
-
-                    def burst():
-                        for _ in range(R):
-                            call()
-                    call_ms = events_ms(burst, 2) / R
-                    stream = torch.cuda.Stream()
-                    graph = torch.cuda.CUDAGraph()
-                    with torch.cuda.stream(stream):
-                        h.bind_stream(stream)
-                        with torch.cuda.graph(graph, stream=stream):
-                            burst()
-                    h.bind_stream()
-                    graph.replay()
-                    torch.cuda.synchronize()
-                    dev_ms = events_ms(graph.replay, 3) / R
-                    reps_per = R
-                    del graph
-                gf = gflop(n, n, n) / (dev_ms * 1e-3)
-                row[var] = {"gflops": round(gf, 2), "dev_us": round(dev_ms * 1e3, 2),
-                            "call_us": round(call_ms * 1e3, 2), "R": reps_per,
-                            "frac": round(gf / peak, 4)}
-            best_plain = max(row["direct"]["gflops"], row["pack_then_compute"]["gflops"])
-            row["fused_over_best_plain"] = round(row["fused"]["gflops"] / best_plain, 4)
-            rows[str(n)] = row
-            del A, B, C
+            vt = VariantTimer(h, g, torch, esz, "N", "N", n, n, n, A, ld, B, ld, BETA, C, ld)
+            at_peak_s = 2.0 * n * n * n / (peak * 1e9)
+            r = rounds if at_peak_s < 0.1 else (long_rounds if at_peak_s < 1.0 else 2)
+            rows[str(n)] = summarize(vt.run(r), gflop(n, n, n), peak)
+            del vt, A, B, C
             torch.cuda.empty_cache()
         out[tag] = rows
     out["status"] = h.status()
+    return out
+
+
+# Configurations beside the square N/N spectrum: the 256^3 workload with every leading
+# dimension exactly 256 (C1), transposed operand orders, beta = 0, unpadded ld.
+EXTRA_CASES = [
+    # (tag, dtype, transa, transb, m, n, k, pad, beta)
+    ("C1 f64 N/N 256 ld=256 beta=0.5", "f64", "N", "N", 256, 256, 256, 0, 0.5),
+    ("f64 T/T 2048 ld=m+7 beta=0", "f64", "T", "T", 2048, 2048, 2048, 7, 0.0),
+    ("f64 N/T 8192x8192x64 ld=m beta=0.5", "f64", "N", "T", 8192, 8192, 64, 0, 0.5),
+    ("f32 T/N 4096 ld=m beta=0", "f32", "T", "N", 4096, 4096, 4096, 0, 0.0),
+    ("f32 N/T 1536 ld=m+7 beta=0.5", "f32", "N", "T", 1536, 1536, 1536, 7, 0.5),
+    ("f32 T/N 64x8192x8192 ld=m+7 beta=0", "f32", "T", "N", 64, 8192, 8192, 7, 0.0),
+]
+
+
+def extra_cases(h, g, torch, rounds=7):
+    out = {}
+    for tag, dt, ta, tb, m, n, k, pad, beta in EXTRA_CASES:
+        dtype = torch.float64 if dt == "f64" else torch.float32
+        esz = 8 if dt == "f64" else 4
+        peak = FP64_PEAK_GFLOPS if dt == "f64" else FP32_PEAK_GFLOPS
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(m + n + k)
+
+        def mat(rows, cols):
+            ld = rows + pad
+            buf = torch.rand((cols, ld), generator=gen, dtype=dtype, device="cuda") * 2 - 1
+            return buf.t()[:rows, :]
+        A = mat(m, k) if ta == "N" else mat(k, m)
+        B = mat(k, n) if tb == "N" else mat(n, k)
+        C = mat(m, n)
+        h.ensure_workspace(ta, tb, m, n, k, esz)
+        vt = VariantTimer(h, g, torch, esz, ta, tb, m, n, k, A, A.stride(1), B, B.stride(1),
+                          beta, C, C.stride(1))
+        out[tag] = summarize(vt.run(rounds), gflop(m, n, k), peak)
+        del vt, A, B, C
     return out
 
 
@@ -340,13 +392,13 @@ def sweep_markdown(res) -> str:
         if tag not in res:
             continue
         lines.append(f"| {tag} n | fused GF/s | direct GF/s | pack-then-compute GF/s | "
-                     "fused / best plain | fused frac of peak | fused dev us | fused call us |")
+                     "fused / best plain | noise | fused frac of peak | fused us |")
         lines.append("|---|---|---|---|---|---|---|---|")
         for n, r in res[tag].items():
-            lines.append(f"| {n} | {r['fused']['gflops']} | {r['direct']['gflops']} | "
-                         f"{r['pack_then_compute']['gflops']} | {r['fused_over_best_plain']} | "
-                         f"{r['fused']['frac']} | {r['fused']['dev_us']} | "
-                         f"{r['fused']['call_us']} |")
+            gf = r["gflops"]
+            lines.append(f"| {n} | {gf['fused']} | {gf['direct']} | {gf['pack_then_compute']} "
+                         f"| {r['fused_over_best_plain']} | {r['noise']} | {r['frac']} | "
+                         f"{r['dev_us']['fused']} |")
         lines.append("")
     return "\n".join(lines)
 
@@ -846,6 +898,47 @@ def run_reference(args, world, rank):
     }), flush=True)
 
 
+def compact_summary(result) -> dict:
+    """The figures a reader needs first, small enough to survive a truncated log tail: per
+    size, [fused GFLOP/s, fused / best plain variant, noise band] in both dtypes, and the
+    headline of each extension report."""
+    out = {}
+    fvp = result.get("fip_vs_plain")
+    if fvp:
+        for tag in ("f64", "f32"):
+            out[f"{tag}_n:[fused_gflops,fused/best_plain,noise]"] = {
+                n: [r["gflops"]["fused"], r["fused_over_best_plain"], r["noise"]]
+                for n, r in fvp[tag].items()}
+        out["extra:[fused/best_plain,noise]"] = {
+            k: [r["fused_over_best_plain"], r["noise"]] for k, r in fvp["extra"].items()}
+        out["min_fused/best_plain-noise"] = round(min(
+            r["fused_over_best_plain"] + r["noise"]
+            for tag in ("f64", "f32") for r in fvp[tag].values()) - 1.0, 4)
+    if "roofline_f32" in result:
+        out["f32_8192_frac_of_ffma_peak"] = result["roofline_f32"]["frac"]
+    emu = result.get("emulated_fp64")
+    if emu:
+        out["emulated_fp64_8192:[S:tflops,max_rel_err_uniform,logmag]"] = {
+            k[len("slices_"):]: [round(v["gflops"] / 1e3, 1), v["max_rel_err"],
+                                 emu["logmag"][k]["max_rel_err"]]
+            for k, v in emu.get("uniform", {}).items()}
+    bat = result.get("batched")
+    if bat:
+        out["batched_4096:[grouped_gflops,frac_of_peak,x_singles]"] = {
+            tag: [v["grouped_graph_gflops"],
+                  round(v["grouped_graph_gflops"] /
+                        (FP64_PEAK_GFLOPS if tag == "f64" else FP32_PEAK_GFLOPS), 4),
+                  v["speedup_vs_singles_graph"]]
+            for tag, v in bat.items() if isinstance(v, dict) and "grouped_graph_gflops" in v}
+    ag = result.get("autograd")
+    if ag:
+        out["autograd:[fused_gflops,x_cublas]"] = {
+            f"{tag} {shape}": [v["fused"], v["fused_over_cublas"]]
+            for tag in ("f64", "f32") for shape, v in ag.get(tag, {}).items()
+            if "fused" in v}
+    return out
+
+
 def main():
     global M, N, K, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -1030,6 +1123,7 @@ def main():
         result["cpu_baseline"] = cpu_oracle_sample(
             bufA.numpy().reshape(-1), bufB.numpy().reshape(-1), bufC.numpy().reshape(-1),
             M, K, lda, ldb, ldc)
+        result["cpu_baseline"]["single_thread"] = oracle_single_thread()
     if rank == 0 and not args.no_emulation:
         result["emulated_fp64"] = emulation_report(
             h, g, torch, slice_counts=tuple(int(x) for x in args.slices.split(",")))
@@ -1042,10 +1136,21 @@ def main():
         result["trmm"] = trmm_report(g, torch)
         result["trsm"] = trsm_report(g, torch)
     if rank == 0 and not args.no_spectrum:
-        result["spectrum_gflops"] = spectrum(h, g, torch)
-        result["spectrum_gflops"]["note"] = ("N/N, ld = m + 7, beta = 0.5, best of a few "
-                                             "launches, CUDA events")
+        from paper_2302_08417_gb300 import inputs
+        clk = ClockSampler(local)
+        clk.start()
+        result["fip_vs_plain"] = sweep(h, g, torch, inputs.config_sizes())
+        result["fip_vs_plain"]["extra"] = extra_cases(h, g, torch)
+        result["fip_vs_plain"]["clocks"] = clk.stop()
+        f32 = result["fip_vs_plain"]["f32"][str(8192)]
+        result["roofline_f32"] = {
+            "bound": "alu", "achieved": f32["gflops"]["fused"], "peak": round(FP32_PEAK_GFLOPS, 1),
+            "unit": "GFLOP/s", "frac": f32["frac"], "traffic": None,
+            "kernel": "gfip::ws::ws_gemm_kernel (FP32, warp-specialised)",
+            "workload": workload("f32", 8192),
+            "peak_basis": "152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"}
     if rank == 0:
+        result["summary"] = compact_summary(result)
         print(json.dumps(result), flush=True)
     if world > 1:
         import torch.distributed as dist

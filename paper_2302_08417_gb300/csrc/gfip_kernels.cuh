@@ -391,12 +391,14 @@ template <typename P> __device__ __forceinline__ int tile_round(const P &p, int 
 template <typename P> __device__ __forceinline__ bool reused_a(const P &p, int i)
 {
     if (p.tri != TRI_NONE || p.shared_pack) return true;
+    if (p.dp_tiles == 0) return false;   // every tile is split: all run in round 0
     return p.nt > 1 && tile_round(p, tile_index(i, p.nt - 1, p.mt, p.nt, p.band)) >
                            tile_round(p, tile_index(i, 0, p.mt, p.nt, p.band));
 }
 template <typename P> __device__ __forceinline__ bool reused_b(const P &p, int j)
 {
     if (p.tri != TRI_NONE || p.shared_pack) return true;
+    if (p.dp_tiles == 0) return false;   // every tile is split: all run in round 0
     return p.mt > 1 && tile_round(p, tile_index(p.mt - 1, j, p.mt, p.nt, p.band)) >
                            tile_round(p, tile_index(0, j, p.mt, p.nt, p.band));
 }
