@@ -307,11 +307,11 @@ class VariantTimer:
         return out
 
 
-def summarize(times, flop, peak):
+def summarize(times, gflop_per_call, peak):
     """Median GFLOP/s per variant, fused / best plain variant, and the noise band: the largest
     relative spread (max - min) / median of the timings of any variant."""
     med = {v: statistics.median(t) for v, t in times.items()}
-    gf = {v: flop / 1e9 / (med[v] * 1e-3) for v in med}
+    gf = {v: gflop_per_call / (med[v] * 1e-3) for v in med}
     noise = max((max(t) - min(t)) / statistics.median(t) for t in times.values())
     best_plain = max(gf["direct"], gf["pack_then_compute"])
     return {"gflops": {v: round(gf[v], 2) for v in VARIANTS},

@@ -561,7 +561,9 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
     }
 
     // C[tile] := alpha*acc + beta*C[tile] (C not read when beta == 0), the operations of the
-    // shared tile core's epilogue, taking C four rows (one 16-byte chunk) at a time.
+    // shared tile core's epilogue.  C is read two columns (32 values) at a time, all loads
+    // issued before any store, so a tile's epilogue costs four round trips to L2 (where the
+    // prefetch at segment start has put C), not one per 4-row chunk.
     static __device__ void epilogue(const GemmParams<float> &p, int i, int j, int tid,
                                     const float (&acc)[TM][TN])
     {
@@ -569,23 +571,32 @@ template <bool ACONTIG, bool BCONTIG> struct WsKernel {
         const int tx = tid % TX, ty = tid / TX;
         const bool read_c = (p.beta != 0.f);
 #pragma unroll
-        for (int jj = 0; jj < TN; ++jj) {
-            const int col = j * 128 + ty * CH + (jj % CH) + (jj / CH) * (128 / NCN);
-            if (col >= p.n) continue;
-            float *ccol = p.C + (int64_t)col * p.ldc;
+        for (int j0 = 0; j0 < TN; j0 += 2) {
+            float cv[2][TM];
 #pragma unroll
-            for (int c = 0; c < TM / CH; ++c) {
-                const int row0 = i * 128 + tx * CH + c * (128 / NCM);
-                float cv[CH];
+            for (int d = 0; d < 2; ++d) {
+                const int jj = j0 + d;
+                const int col = j * 128 + ty * CH + (jj % CH) + (jj / CH) * (128 / NCN);
+                const float *ccol = p.C + (int64_t)col * p.ldc;
 #pragma unroll
-                for (int r = 0; r < CH; ++r)
-                    cv[r] = (read_c && row0 + r < p.m) ? ccol[row0 + r] : 0.f;
+                for (int ii = 0; ii < TM; ++ii) {
+                    const int row = i * 128 + tx * CH + (ii % CH) + (ii / CH) * (128 / NCM);
+                    cv[d][ii] = (read_c && col < p.n && row < p.m) ? ccol[row] : 0.f;
+                }
+            }
 #pragma unroll
-                for (int r = 0; r < CH; ++r) {
-                    if (row0 + r >= p.m) continue;
-                    float v = p.alpha * acc[c * CH + r][jj];
-                    if (read_c) v = fmaf(p.beta, cv[r], v);
-                    ccol[row0 + r] = v;
+            for (int d = 0; d < 2; ++d) {
+                const int jj = j0 + d;
+                const int col = j * 128 + ty * CH + (jj % CH) + (jj / CH) * (128 / NCN);
+                if (col >= p.n) continue;
+                float *ccol = p.C + (int64_t)col * p.ldc;
+#pragma unroll
+                for (int ii = 0; ii < TM; ++ii) {
+                    const int row = i * 128 + tx * CH + (ii % CH) + (ii / CH) * (128 / NCM);
+                    if (row >= p.m) continue;
+                    float v = p.alpha * acc[ii][jj];
+                    if (read_c) v = fmaf(p.beta, cv[d][ii], v);
+                    ccol[row] = v;
                 }
             }
         }
