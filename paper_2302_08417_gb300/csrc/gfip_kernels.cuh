@@ -290,11 +290,11 @@ __device__ __forceinline__ unsigned long long ready_value(unsigned int epoch)
 }
 
 // Publishes a packed tile.  Called by thread 0 after a CTA barrier that follows every
-// thread's pack stores of that tile; the fence and the release make them visible first.
+// thread's pack stores of that tile: the release store is cumulative, so the stores the
+// barrier ordered before it are visible to any thread that acquires the word.
 __device__ __forceinline__ void publish(unsigned long long *word, unsigned int epoch)
 {
     const unsigned long long v = (static_cast<unsigned long long>(epoch) << 32) | 1ull;
-    __threadfence();
     asm volatile("st.release.gpu.global.u64 [%0], %1;\n" ::"l"(word), "l"(v) : "memory");
 }
 
