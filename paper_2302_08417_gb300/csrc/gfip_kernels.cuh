@@ -407,9 +407,9 @@ template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     using Cfg = C;
     T a[Cfg::STAGES][TileLayout<T, Cfg::BM, Cfg::BK>::ELEMS];
     T b[Cfg::STAGES][TileLayout<T, Cfg::BN, Cfg::BK>::ELEMS];
-    int dec_a[2 * Cfg::STAGES];
-    int dec_b[2 * Cfg::STAGES];
-    int part[2 * Cfg::STAGES];   // bit 0 (1): the A (B) block is cut by a triangular mask
+    int dec_a[4 * Cfg::STAGES];
+    int dec_b[4 * Cfg::STAGES];
+    int part[4 * Cfg::STAGES];   // bit 0 (1): the A (B) block is cut by a triangular mask
     int full_a, full_b;  // the tile's whole A (B) panel is already published
     int mode_a, mode_b;  // the segment's operand modes after the reuse logic (reused_a/_b)
     int watch;           // shared packing: the count of packed tiles is not complete yet
@@ -449,7 +449,8 @@ struct Kernel {
     static_assert(TX * (BN / TN) == THREADS, "thread grid must cover the tile");
     static_assert(NCN == 1 || NCN == 2, "one or two chunks along n");
     static_assert(NCM == 2 || NCM == 4, "two or four chunks along m");
-    static constexpr int DEC = 2 * STAGES;
+    static constexpr int DEC = 4 * STAGES;   // decision ring: STAGES ahead, PUB behind
+    static constexpr int PUB = 4;            // k-blocks a producer publishes per fence
     using LoadA = RawLoader<T, BM, BK, THREADS, ACONTIG>;
     using LoadB = RawLoader<T, BN, BK, THREADS, BCONTIG>;
     using AccT = T[TM][TN];
@@ -673,15 +674,34 @@ struct Kernel {
                (2ull * static_cast<unsigned long long>(p.pack_units));
     }
 
-    // Publishes the tiles this CTA produced at local k-block it (thread 0 only).
+    // Publishes the tiles this CTA produced at local k-blocks it0 .. it1 - 1 (thread 0 only,
+    // after a CTA barrier that follows their pack stores): one release fence for the whole
+    // range, then relaxed stores of the ready words.  Batching PUB k-blocks per fence keeps
+    // the fence, which stalls warp 0 until its earlier memory operations are done, off most
+    // k-blocks; only tiles running beside the producer could use a finer grain.
     static __device__ __forceinline__ void publish_produced(const GemmParams<T> &p,
                                                             const Smem &sm, int i, int j,
-                                                            int kb0, int it, unsigned int epoch)
+                                                            int kb0, int it0, int it1,
+                                                            unsigned int epoch)
     {
-        if (sm.dec_a[it % DEC] == DEC_PRODUCE)
-            publish(p.state_a + (int64_t)i * p.kt + kb0 + it, epoch);
-        if (sm.dec_b[it % DEC] == DEC_PRODUCE)
-            publish(p.state_b + (int64_t)j * p.kt + kb0 + it, epoch);
+        bool any = false;
+        for (int it = it0; it < it1; ++it)
+            any |= sm.dec_a[it % DEC] == DEC_PRODUCE || sm.dec_b[it % DEC] == DEC_PRODUCE;
+        if (!any) return;
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        const unsigned long long v = ready_value(epoch);
+        for (int it = it0; it < it1; ++it) {
+            if (sm.dec_a[it % DEC] == DEC_PRODUCE)
+                asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(
+                                 p.state_a + (int64_t)i * p.kt + kb0 + it),
+                             "l"(v)
+                             : "memory");
+            if (sm.dec_b[it % DEC] == DEC_PRODUCE)
+                asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(
+                                 p.state_b + (int64_t)j * p.kt + kb0 + it),
+                             "l"(v)
+                             : "memory");
+        }
     }
 
     // Accumulates op(A)[tile rows, kb0*BK : kb1*BK] * op(B)[..., tile cols] into acc, packing
@@ -799,15 +819,15 @@ struct Kernel {
                 }
                 if (ahead && store_decisions(p, sm, i, j, kb0 + it + STAGES, w, it + STAGES, epoch))
                     fence_acquire();
-                // the pack stores of the previous k-block were ordered by this iteration's
-                // barrier and have drained during the compute
-                if (it > 0) publish_produced(p, sm, i, j, kb0, it - 1, epoch);
+                // the pack stores of the previous PUB k-blocks were ordered by this
+                // iteration's barrier and have drained during the compute
+                if (it > 0 && it % PUB == 0) publish_produced(p, sm, i, j, kb0, it - PUB, it, epoch);
             }
         }
         cp_async_wait<0>();
         __syncthreads();
         if (tid == 0 && nkb > 0) {
-            publish_produced(p, sm, i, j, kb0, nkb - 1, epoch);
+            publish_produced(p, sm, i, j, kb0, ((nkb - 1) / PUB) * PUB, nkb, epoch);
             // a producer that covered its whole panel publishes the panel as complete
             if (kb0 == 0 && kb1 == p.kt) {
                 if (sm.mode_a == MODE_FIP && prod_a(p, j))
