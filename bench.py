@@ -501,8 +501,10 @@ def batched_report(g, torch, count=4096, seed=11):
             C.append(mk(m, n, pads[q, 2]))
         batch = gr.Batch(list(ta), list(tb), A, B, C, [1.0] * count, [BETA] * count)
         flops = batch.flops()
-        tile = gr.autotune(batch)
-        runner = gr.GraphRunner(batch, tile)
+        t0 = time.perf_counter()
+        plan = gr.autotune_plan(batch)
+        tune_s = time.perf_counter() - t0
+        runner = gr.GraphRunner(batch, plan)
 
         def timed(fn, reps=5):
             fn()
@@ -545,8 +547,15 @@ def batched_report(g, torch, count=4096, seed=11):
         h.bind_stream()
         singles_graph_ms = timed(graph.replay)
         singles_eager_ms = timed(singles, reps=2)
-        out[tag] = {"tile": int(tile), "gflop_per_batch": round(flops / 1e9, 3),
-                    "grouped_graph_gflops": round(flops / 1e9 / (grouped_ms * 1e-3), 1),
+        choice = gr._tuned.get(batch.signature(), {})
+        peak = FP64_PEAK_GFLOPS if tag == "f64" else FP32_PEAK_GFLOPS
+        gf_grouped = flops / 1e9 / (grouped_ms * 1e-3)
+        out[tag] = {"plan": {f"{b[0]}/{b[1]}": list(v) for b, v in sorted(choice.items())},
+                    "plan_note": "size bucket (max(m,n) class <=16,32,64,128,more / k class "
+                                 "<32,<128,more) -> [tile shape, k-splits]",
+                    "tune_s": round(tune_s, 2), "gflop_per_batch": round(flops / 1e9, 3),
+                    "grouped_graph_gflops": round(gf_grouped, 1),
+                    "frac_of_peak": round(gf_grouped / peak, 4),
                     "singles_graph_gflops": round(flops / 1e9 / (singles_graph_ms * 1e-3), 1),
                     "singles_eager_gflops": round(flops / 1e9 / (singles_eager_ms * 1e-3), 1),
                     "grouped_ms": round(grouped_ms, 3),

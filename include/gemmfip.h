@@ -247,15 +247,33 @@ int gfip_strsm(gfip_handle_t handle, char side, char uplo, char transa, char dia
  * with per-problem transa[g], transb[g] ('N','T','C'), m[g], n[g], k[g], leading dimensions and
  * matrix pointers.  EVERY array argument is a DEVICE array of `count` entries (the pointer
  * arrays hold device pointers), so the call reads nothing on the host and can be captured in
- * a CUDA graph: it enqueues a preparation kernel, a prefix-sum kernel and one persistent
- * GEMM kernel on the handle's stream.  Each problem follows the reference-BLAS rules of
- * gfip_dgemm; a problem with invalid arguments is skipped (its C untouched) and raises
- * GFIP_STATUS_BAD_PROBLEM.  `tile` selects the tile shape (GFIP_GROUP_TILE_*: chosen by the
- * Python autotuner); FP64 has one tile shape.  Needs gfip_grouped_workspace_size() bytes of
- * workspace.  Returns GFIP_ERR_ARG for count < 0 or an unknown tile. */
-#define GFIP_GROUP_TILE_DEFAULT 0   /* the single-GEMM tile (FP32 128 x 128, FP64 32 x 32)  */
-#define GFIP_GROUP_TILE_SMALL 1     /* FP32 64 x 64 tile for small problems                 */
+ * a CUDA graph (after one eager call on the handle's workspace, see GFIP_ERR_CAPTURE): it
+ * enqueues a preparation kernel, a prefix-sum kernel and one persistent GEMM kernel on the
+ * handle's stream.  The unit of work is one warp computing one small tile of one problem, so
+ * one launch runs problems of different tile shapes side by side.  Each problem follows the
+ * reference-BLAS rules of gfip_dgemm; a problem with invalid arguments is skipped (its C
+ * untouched) and raises GFIP_STATUS_BAD_PROBLEM.
+ *
+ * gfip_?gemm_grouped: every problem takes the warp tile `tile` (GFIP_GROUP_TILE_*), unsplit.
+ * Needs gfip_grouped_workspace_size() bytes of workspace.  GFIP_ERR_ARG for count < 0 or an
+ * unknown tile.
+ *
+ * gfip_?gemm_grouped_plan: problem g takes plan[g] = GFIP_GROUP_PLAN(tile, splits) (a device
+ * array): its warp tile, and the number of k-ranges (1..8) each of its tiles is split into,
+ * computed by different warps and added in k-range order by the last to finish (the result
+ * bits depend on the plan, never on timing).  `order` (a device array, or NULL for 0..count-1)
+ * is the processing order of the problems, e.g. largest first.  split_elems is the number of
+ * partial-sum elements the plan needs (the sum over split problems of tiles x splits x tile
+ * area); the workspace must hold gfip_grouped_plan_workspace_size(count, split_elems) bytes,
+ * and a problem whose partial sums would not fit runs unsplit.  The plan is chosen per size
+ * bucket by the Python autotuner (grouped.autotune_plan). */
+#define GFIP_GROUP_TILE_DEFAULT 0   /* warp tile FP32 64 x 32, FP64 32 x 32                     */
+#define GFIP_GROUP_TILE_SMALL 1     /* warp tile FP32 32 x 32, FP64 32 x 16                     */
+#define GFIP_GROUP_TILE_TINY 2      /* warp tile 16 x 16                                        */
+#define GFIP_GROUP_PLAN(tile, splits) ((tile) | ((splits) << 8))
 size_t gfip_grouped_workspace_size(gfip_handle_t handle, int count);
+size_t gfip_grouped_plan_workspace_size(gfip_handle_t handle, int count, int64_t split_elems,
+                                        int elem_bytes);
 int gfip_dgemm_grouped(gfip_handle_t handle, int count, const char *transa, const char *transb,
                        const int *m, const int *n, const int *k, const double *alpha,
                        const double *const *A, const int64_t *lda, const double *const *B,
@@ -266,6 +284,18 @@ int gfip_sgemm_grouped(gfip_handle_t handle, int count, const char *transa, cons
                        const float *const *A, const int64_t *lda, const float *const *B,
                        const int64_t *ldb, const float *beta, float *const *C,
                        const int64_t *ldc, int tile);
+int gfip_dgemm_grouped_plan(gfip_handle_t handle, int count, const char *transa,
+                            const char *transb, const int *m, const int *n, const int *k,
+                            const double *alpha, const double *const *A, const int64_t *lda,
+                            const double *const *B, const int64_t *ldb, const double *beta,
+                            double *const *C, const int64_t *ldc, const int *plan,
+                            const int *order, int64_t split_elems);
+int gfip_sgemm_grouped_plan(gfip_handle_t handle, int count, const char *transa,
+                            const char *transb, const int *m, const int *n, const int *k,
+                            const float *alpha, const float *const *A, const int64_t *lda,
+                            const float *const *B, const int64_t *ldb, const float *beta,
+                            float *const *C, const int64_t *ldc, const int *plan,
+                            const int *order, int64_t split_elems);
 
 /* Waits for the handle's stream, then returns the OR of the device status bits
  * (GFIP_STATUS_*) raised since the previous call of this function, and clears them.

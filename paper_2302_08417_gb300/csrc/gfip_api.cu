@@ -413,6 +413,38 @@ OzPlan oz_plan(int64_t m, int64_t n, int64_t k, int slices)
     return o;
 }
 
+// Workspace layout of a grouped launch (after the control region): descriptors, per-rank
+// units / split tiles / partial-sum elements, prefix sums, arrival counters, partial sums.
+struct GroupedLayout {
+    size_t desc = 0, units = 0, stiles = 0, pelems = 0, prefix = 0, counters = 0, partial = 0;
+    size_t bytes = 0;
+    int max_split_tiles = 0;
+};
+
+GroupedLayout grouped_layout(int count, int64_t split_elems, int es)
+{
+    GroupedLayout l;
+    size_t d = 0;
+    l.desc = d;
+    d += round_up(gfip::grouped_desc_bytes(count, es), kAlign);
+    l.units = d;
+    d += round_up((size_t)count * sizeof(int), kAlign);
+    l.stiles = d;
+    d += round_up((size_t)count * sizeof(int), kAlign);
+    l.pelems = d;
+    d += round_up((size_t)count * sizeof(int64_t), kAlign);
+    l.prefix = d;
+    d += round_up(((size_t)count + 1) * sizeof(int), kAlign);
+    // a split tile holds at least 2 x 16 x 16 partial sums
+    l.max_split_tiles = static_cast<int>(std::min<int64_t>(split_elems / 512, 1 << 30));
+    l.counters = d;
+    d += round_up((size_t)l.max_split_tiles * sizeof(int) + sizeof(int), kAlign);
+    l.partial = d;
+    d += round_up((size_t)split_elems * es, kAlign);
+    l.bytes = d;
+    return l;
+}
+
 template <typename T>
 size_t workspace_size_impl(Handle *h, char transa, char transb, int64_t m, int64_t n, int64_t k,
                            Variant v)
@@ -982,9 +1014,7 @@ size_t gfip_grouped_workspace_size(gfip_handle_t handle, int count)
 {
     Handle *h = get(handle);
     if (h == nullptr || count < 0) return 0;
-    const size_t desc = round_up((size_t)count * sizeof(gfip::GroupDesc<double>), kAlign);
-    const size_t pre = round_up(((size_t)count + 1) * sizeof(int), kAlign);
-    return std::max(h->ctrl_bytes, kCtrlGranule) + desc + pre;
+    return std::max(h->ctrl_bytes, kCtrlGranule) + grouped_layout(count, 0, 8).bytes;
 }
 
 size_t gfip_ozaki_workspace_size(gfip_handle_t handle, int64_t m, int64_t n, int64_t k,
@@ -1067,11 +1097,13 @@ template <typename T>
 int grouped_entry(gfip_handle_t handle, int count, const char *transa, const char *transb,
                   const int *m, const int *n, const int *k, const T *alpha, const T *const *A,
                   const int64_t *lda, const T *const *B, const int64_t *ldb, const T *beta,
-                  T *const *C, const int64_t *ldc, int tile)
+                  T *const *C, const int64_t *ldc, int tile, const int *plan, const int *order,
+                  int64_t split_elems)
 {
     Handle *h = get(handle);
     if (h == nullptr) return GFIP_ERR_HANDLE;
-    if (count < 0 || tile < GFIP_GROUP_TILE_DEFAULT || tile > GFIP_GROUP_TILE_SMALL)
+    if (count < 0 || tile < GFIP_GROUP_TILE_DEFAULT || tile > GFIP_GROUP_TILE_TINY ||
+        split_elems < 0)
         return GFIP_ERR_ARG;
     h->last_launches = 0;
     h->last_grid = 0;
@@ -1080,10 +1112,9 @@ int grouped_entry(gfip_handle_t handle, int count, const char *transa, const cha
         !C || !ldc)
         return GFIP_ERR_NULLPTR;
     if (h->ws == nullptr) return GFIP_ERR_WORKSPACE;
-    const size_t desc = round_up((size_t)count * sizeof(gfip::GroupDesc<T>), kAlign);
-    const size_t pre = round_up(((size_t)count + 1) * sizeof(int), kAlign);
+    const GroupedLayout l = grouped_layout(count, split_elems, static_cast<int>(sizeof(T)));
     const size_t ctrl_want = std::max(h->ctrl_bytes, kCtrlGranule);
-    if (ctrl_want + desc + pre > h->ws_bytes) return GFIP_ERR_WORKSPACE;
+    if (ctrl_want + l.bytes > h->ws_bytes) return GFIP_ERR_WORKSPACE;
     if (const int rc = grow_ctrl(h, ctrl_want); rc != GFIP_OK) return rc;
     unsigned char *data = h->ws + h->ctrl_bytes;
     gfip::GroupParams<T> gp{};
@@ -1101,10 +1132,20 @@ int grouped_entry(gfip_handle_t handle, int count, const char *transa, const cha
     gp.lda = lda;
     gp.ldb = ldb;
     gp.ldc = ldc;
-    gp.desc = reinterpret_cast<gfip::GroupDesc<T> *>(data);
-    gp.prefix = reinterpret_cast<int *>(data + desc);
+    gp.plan = plan;
+    gp.order = order;
+    gp.uniform_shape = tile;
+    gp.desc = reinterpret_cast<gfip::GroupDesc<T> *>(data + l.desc);
+    gp.units = reinterpret_cast<int *>(data + l.units);
+    gp.stiles = reinterpret_cast<int *>(data + l.stiles);
+    gp.pelems = reinterpret_cast<int64_t *>(data + l.pelems);
+    gp.prefix = reinterpret_cast<int *>(data + l.prefix);
+    gp.counters = reinterpret_cast<int *>(data + l.counters);
+    gp.max_split_tiles = l.max_split_tiles;
+    gp.partial = reinterpret_cast<T *>(data + l.partial);
+    gp.partial_capacity = split_elems;
     gp.status = reinterpret_cast<unsigned int *>(h->ws);
-    if (gfip::launch_grouped<T>(gp, tile, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
+    if (gfip::launch_grouped<T>(gp, h->stream) != cudaSuccess) return GFIP_ERR_CUDA;
     h->last_launches = 3;
     return GFIP_OK;
 }
@@ -1120,7 +1161,7 @@ int gfip_dgemm_grouped(gfip_handle_t handle, int count, const char *transa, cons
                        const int64_t *ldc, int tile)
 {
     return grouped_entry<double>(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb,
-                                 beta, C, ldc, tile);
+                                 beta, C, ldc, tile, nullptr, nullptr, 0);
 }
 
 int gfip_sgemm_grouped(gfip_handle_t handle, int count, const char *transa, const char *transb,
@@ -1130,7 +1171,41 @@ int gfip_sgemm_grouped(gfip_handle_t handle, int count, const char *transa, cons
                        const int64_t *ldc, int tile)
 {
     return grouped_entry<float>(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb,
-                                beta, C, ldc, tile);
+                                beta, C, ldc, tile, nullptr, nullptr, 0);
+}
+
+size_t gfip_grouped_plan_workspace_size(gfip_handle_t handle, int count, int64_t split_elems,
+                                        int elem_bytes)
+{
+    Handle *h = get(handle);
+    if (h == nullptr || count < 0 || split_elems < 0 || (elem_bytes != 4 && elem_bytes != 8))
+        return 0;
+    return std::max(h->ctrl_bytes, kCtrlGranule) +
+           grouped_layout(count, split_elems, elem_bytes).bytes;
+}
+
+int gfip_dgemm_grouped_plan(gfip_handle_t handle, int count, const char *transa,
+                            const char *transb, const int *m, const int *n, const int *k,
+                            const double *alpha, const double *const *A, const int64_t *lda,
+                            const double *const *B, const int64_t *ldb, const double *beta,
+                            double *const *C, const int64_t *ldc, const int *plan,
+                            const int *order, int64_t split_elems)
+{
+    if (plan == nullptr) return GFIP_ERR_NULLPTR;
+    return grouped_entry<double>(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb,
+                                 beta, C, ldc, 0, plan, order, split_elems);
+}
+
+int gfip_sgemm_grouped_plan(gfip_handle_t handle, int count, const char *transa,
+                            const char *transb, const int *m, const int *n, const int *k,
+                            const float *alpha, const float *const *A, const int64_t *lda,
+                            const float *const *B, const int64_t *ldb, const float *beta,
+                            float *const *C, const int64_t *ldc, const int *plan,
+                            const int *order, int64_t split_elems)
+{
+    if (plan == nullptr) return GFIP_ERR_NULLPTR;
+    return grouped_entry<float>(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb,
+                                beta, C, ldc, 0, plan, order, split_elems);
 }
 
 }  // extern "C"

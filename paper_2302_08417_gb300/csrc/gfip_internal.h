@@ -164,12 +164,13 @@ cudaError_t launch_trsm_diag(T *B, int64_t vstride, int64_t estride, int nvec, c
                              int64_t lda, int a_trans, int k0, int nb, int lower_t,
                              int transpose_t, int unit, cudaStream_t s);
 
-// Grouped GEMM (gfip_grouped.cu): many independent problems in one persistent launch.
-enum GroupTile : int { GROUP_TILE_DEFAULT = 0, GROUP_TILE_SMALL = 1 };
+// Grouped GEMM (gfip_grouped.cu): many independent problems in one persistent launch, each
+// problem with its own warp-tile shape and k-split factor.
 template <typename T> struct GroupDesc;
 template <typename T> struct GroupParams;
-template <typename T>
-cudaError_t launch_grouped(const GroupParams<T> &gp, int tile, cudaStream_t s);
+template <typename T> cudaError_t launch_grouped(const GroupParams<T> &gp, cudaStream_t s);
+// Bytes of one grouped launch's descriptor arrays for `count` problems (element size es).
+size_t grouped_desc_bytes(int count, int es);
 
 // Launchers (defined per element type in gfip_f64.cu / gfip_f32.cu).
 template <typename T> cudaError_t launch_gemm(const GemmParams<T> &p, cudaStream_t s);

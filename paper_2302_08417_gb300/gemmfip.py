@@ -33,7 +33,11 @@ GFIP_STATUS_BAD_SEGMENT = 0x1
 GFIP_STATUS_MMA_TIMEOUT = 0x2
 GFIP_STATUS_BAD_PROBLEM = 0x4
 GFIP_STATUS_WAIT_TIMEOUT = 0x8
-GFIP_GROUP_TILE_DEFAULT, GFIP_GROUP_TILE_SMALL = 0, 1
+GFIP_GROUP_TILE_DEFAULT, GFIP_GROUP_TILE_SMALL, GFIP_GROUP_TILE_TINY = 0, 1, 2
+
+
+def GFIP_GROUP_PLAN(tile: int, splits: int) -> int:
+    return tile | (splits << 8)
 
 GFIP_PACK_AUTO, GFIP_PACK_NONE, GFIP_PACK_A, GFIP_PACK_B, GFIP_PACK_BOTH = range(5)
 GFIP_PACKER_AUTO, GFIP_PACKER_LINE, GFIP_PACKER_SHARED = range(3)
@@ -66,6 +70,9 @@ SIGNATURES = {
     "gfip_grouped_workspace_size": (_sz, [_ptr, _int]),
     "gfip_dgemm_grouped": (_int, [_ptr, _int] + [_ptr] * 13 + [_int]),
     "gfip_sgemm_grouped": (_int, [_ptr, _int] + [_ptr] * 13 + [_int]),
+    "gfip_grouped_plan_workspace_size": (_sz, [_ptr, _int, _i64, _int]),
+    "gfip_dgemm_grouped_plan": (_int, [_ptr, _int] + [_ptr] * 15 + [_i64]),
+    "gfip_sgemm_grouped_plan": (_int, [_ptr, _int] + [_ptr] * 15 + [_i64]),
     "gfip_dgemm_ozaki": (_int, _GEMM_D + [_int]),
     "gfip_debug_ozaki_timeout": (_int, [_ptr, _int, ctypes.c_uint64]),
     "gfip_syrk_workspace_size": (_sz, [_ptr, _chr, _chr, _i64, _i64, _int]),
@@ -265,6 +272,18 @@ def gfip_gemm_grouped(esz, handle, count, transa, transb, m, n, k, alpha, A, lda
     """Grouped GEMM; every array argument is a device pointer (int)."""
     fn = load().gfip_dgemm_grouped if esz == 8 else load().gfip_sgemm_grouped
     return fn(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tile)
+
+
+def gfip_grouped_plan_workspace_size(handle, count, split_elems, elem_bytes) -> int:
+    return load().gfip_grouped_plan_workspace_size(handle, count, split_elems, elem_bytes)
+
+
+def gfip_gemm_grouped_plan(esz, handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb,
+                           beta, C, ldc, plan, order, split_elems) -> int:
+    """Grouped GEMM with a per-problem plan; array arguments are device pointers (int)."""
+    fn = load().gfip_dgemm_grouped_plan if esz == 8 else load().gfip_sgemm_grouped_plan
+    return fn(handle, count, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, plan,
+              order or None, split_elems)
 
 
 ENTRY = {

@@ -1,21 +1,29 @@
 """Grouped GEMM: a batch of independent problems of uneven sizes as one launch.
 
-:class:`Batch` holds the device arrays the C entry points ``gfip_dgemm_grouped`` /
-``gfip_sgemm_grouped`` read (problem sizes, operand orders, leading dimensions, scalars and
-device pointers), :func:`autotune` picks the tile shape for a batch by timing every compiled
-shape on that batch (results cached by a size signature), and :class:`GraphRunner` captures
-the call in a CUDA graph and replays it.  All arithmetic runs in the CUDA library.
+:class:`Batch` holds the device arrays the C entry points read (problem sizes, operand orders,
+leading dimensions, scalars, device pointers, and a processing order, largest problems first).
+A :class:`Plan` gives each problem a warp-tile shape and a k-split factor; plans are chosen
+per size bucket by :func:`autotune_plan`, which times candidate plans on the batch itself
+(coordinate descent over the buckets, on scratch copies of C, whatever beta is) and caches the
+choice by the batch's size histogram.  :class:`GraphRunner` captures the call in a CUDA graph
+and replays it.  All arithmetic runs in the CUDA library.
 """
 from __future__ import annotations
 
 import math
+import statistics
 
 import torch
 
 from . import gemmfip as g
 
-TILES = {8: (g.GFIP_GROUP_TILE_DEFAULT,),
-         4: (g.GFIP_GROUP_TILE_DEFAULT, g.GFIP_GROUP_TILE_SMALL)}
+TILES = {8: (g.GFIP_GROUP_TILE_DEFAULT, g.GFIP_GROUP_TILE_SMALL, g.GFIP_GROUP_TILE_TINY),
+         4: (g.GFIP_GROUP_TILE_DEFAULT, g.GFIP_GROUP_TILE_SMALL, g.GFIP_GROUP_TILE_TINY)}
+# warp tile (rows x columns of C) of each tile shape, per element size
+SHAPES = {(4, 0): (64, 32), (4, 1): (32, 32), (4, 2): (16, 16),
+          (8, 0): (32, 32), (8, 1): (32, 16), (8, 2): (16, 16)}
+SPLITS = (1, 2, 4)
+KC = 16   # k rows per chunk of the warp pipeline
 
 
 class Batch:
@@ -34,6 +42,7 @@ class Batch:
         dev = A[0].device if count else torch.device("cuda")
         self.count = count
         self.dtype = dtype
+        self.device = dev
         self.esz = 8 if dtype == torch.float64 else 4
         ms, ns, ks = [], [], []
         for ta, tb, a, b in zip(transa, transb, A, B):
@@ -52,6 +61,8 @@ class Batch:
 
         i32 = dict(dtype=torch.int32, device=dev)
         i64 = dict(dtype=torch.int64, device=dev)
+        self._args = dict(transa=list(transa), transb=list(transb), alpha=list(alpha),
+                          beta=list(beta))
         self.transa = torch.tensor([ord(t) for t in transa], dtype=torch.uint8, device=dev)
         self.transb = torch.tensor([ord(t) for t in transb], dtype=torch.uint8, device=dev)
         self.m = torch.tensor(ms, **i32)
@@ -65,34 +76,97 @@ class Batch:
         self.lda = torch.tensor([ld(x) for x in A], **i64)
         self.ldb = torch.tensor([ld(x) for x in B], **i64)
         self.ldc = torch.tensor([ld(x) for x in C], **i64)
+        # processing order: largest problems first, so the persistent warps end together
+        rank = sorted(range(count), key=lambda q: -ms[q] * ns[q] * max(ks[q], 1))
+        self.order = torch.tensor(rank, **i32)
         self._keep = (A, B, C)   # the operands must outlive the batch
 
     def flops(self) -> float:
         return sum(2.0 * m * n * k for m, n, k in self.sizes)
 
+    def with_scratch_c(self) -> "Batch":
+        """The same problems writing to fresh copies of C (for timing candidate plans)."""
+        A, B, C = self._keep
+        Cs = []
+        for c in C:
+            buf = torch.empty((c.shape[1], c.stride(1)), dtype=c.dtype, device=c.device)
+            view = buf.t()[: c.shape[0], :]
+            view.copy_(c)
+            Cs.append(view)
+        return Batch(self._args["transa"], self._args["transb"], A, B, Cs, self._args["alpha"],
+                     self._args["beta"])
+
     def signature(self):
-        """Size bucket of the batch: dtype, count, log2 buckets of the median m, n, k."""
-        def med(i):
-            v = sorted(s[i] for s in self.sizes)
-            return int(math.log2(max(1, v[len(v) // 2]))) if v else 0
-        return (self.esz, self.count, med(0), med(1), med(2))
+        """Size histogram of the batch: dtype, count and the problem count per size bucket."""
+        hist = {}
+        for m, n, k in self.sizes:
+            b = bucket_of(m, n, k)
+            hist[b] = hist.get(b, 0) + 1
+        return (self.esz, self.count, tuple(sorted(hist.items())))
 
 
-def run(batch: Batch, tile: int, handle: g.Handle | None = None) -> None:
-    """Enqueues the grouped GEMM on torch's current stream (asynchronous)."""
-    h = handle or g.default_handle()
-    h.bind_stream()
-    need = g.gfip_grouped_workspace_size(h.h, batch.count)
+def bucket_of(m: int, n: int, k: int):
+    """Size bucket of a problem: class of max(m, n) (<= 16, 32, 64, 128, more) and of k
+    (< 32, < 128, more)."""
+    x = max(m, n)
+    sc = 0 if x <= 16 else 1 if x <= 32 else 2 if x <= 64 else 3 if x <= 128 else 4
+    kc = 0 if k < 32 else 1 if k < 128 else 2
+    return (sc, kc)
+
+
+class Plan:
+    """Warp-tile shape and k-split factor per problem, as the device array the library reads."""
+
+    def __init__(self, batch: Batch, codes):
+        self.codes = list(codes)
+        self.tensor = torch.tensor(self.codes, dtype=torch.int32, device=batch.device)
+        self.split_elems = 0
+        for (m, n, k), c in zip(batch.sizes, self.codes):
+            tile, splits = c & 0xFF, c >> 8
+            bm, bn = SHAPES[(batch.esz, tile)]
+            splits = max(1, min(splits, math.ceil(max(k, 1) / KC)))
+            if splits > 1 and m > 0 and n > 0:
+                self.split_elems += math.ceil(m / bm) * math.ceil(n / bn) * splits * bm * bn
+
+    @classmethod
+    def from_buckets(cls, batch: Batch, choice: dict) -> "Plan":
+        return cls(batch, [g.GFIP_GROUP_PLAN(*choice[bucket_of(*s)]) for s in batch.sizes])
+
+    @classmethod
+    def uniform(cls, batch: Batch, tile: int, splits: int = 1) -> "Plan":
+        return cls(batch, [g.GFIP_GROUP_PLAN(tile, splits)] * batch.count)
+
+
+def _ensure(h, need):
     if h.workspace is None or h.workspace.numel() < need:
         if h.workspace is not None:
             torch.cuda.current_stream().synchronize()
         h._set_ws(need + (1 << 20))
-    rc = g.gfip_gemm_grouped(batch.esz, h.h, batch.count, batch.transa.data_ptr(),
-                             batch.transb.data_ptr(), batch.m.data_ptr(), batch.n.data_ptr(),
-                             batch.k.data_ptr(), batch.alpha.data_ptr(), batch.A.data_ptr(),
-                             batch.lda.data_ptr(), batch.B.data_ptr(), batch.ldb.data_ptr(),
-                             batch.beta.data_ptr(), batch.C.data_ptr(), batch.ldc.data_ptr(),
-                             tile)
+
+
+def run(batch: Batch, tile_or_plan, handle: g.Handle | None = None) -> None:
+    """Enqueues the grouped GEMM on torch's current stream (asynchronous): every problem with
+    one tile shape (an int, GFIP_GROUP_TILE_*), or with the shapes and splits of a Plan."""
+    h = handle or g.default_handle()
+    h.bind_stream()
+    if isinstance(tile_or_plan, Plan):
+        plan = tile_or_plan
+        _ensure(h, g.gfip_grouped_plan_workspace_size(h.h, batch.count, plan.split_elems,
+                                                       batch.esz))
+        rc = g.gfip_gemm_grouped_plan(
+            batch.esz, h.h, batch.count, batch.transa.data_ptr(), batch.transb.data_ptr(),
+            batch.m.data_ptr(), batch.n.data_ptr(), batch.k.data_ptr(), batch.alpha.data_ptr(),
+            batch.A.data_ptr(), batch.lda.data_ptr(), batch.B.data_ptr(), batch.ldb.data_ptr(),
+            batch.beta.data_ptr(), batch.C.data_ptr(), batch.ldc.data_ptr(),
+            plan.tensor.data_ptr(), batch.order.data_ptr(), plan.split_elems)
+    else:
+        _ensure(h, g.gfip_grouped_workspace_size(h.h, batch.count))
+        rc = g.gfip_gemm_grouped(batch.esz, h.h, batch.count, batch.transa.data_ptr(),
+                                 batch.transb.data_ptr(), batch.m.data_ptr(), batch.n.data_ptr(),
+                                 batch.k.data_ptr(), batch.alpha.data_ptr(), batch.A.data_ptr(),
+                                 batch.lda.data_ptr(), batch.B.data_ptr(), batch.ldb.data_ptr(),
+                                 batch.beta.data_ptr(), batch.C.data_ptr(),
+                                 batch.ldc.data_ptr(), int(tile_or_plan))
     if rc != g.GFIP_OK:
         raise g.GemmError(rc, "gfip_gemm_grouped")
 
@@ -100,42 +174,82 @@ def run(batch: Batch, tile: int, handle: g.Handle | None = None) -> None:
 def run_batch(transa, transb, A, B, C, alpha, tile=None, beta=0.0,
               handle: g.Handle | None = None) -> Batch:
     """C_g := alpha op(A_g) op(B_g) + beta C_g for lists of column-major tensors, as one
-    grouped launch; ``tile`` None asks :func:`autotune` (which, with beta == 0, may overwrite
-    C while timing).  Returns the batch (it keeps the operands alive)."""
+    grouped launch; ``tile`` None asks :func:`autotune_plan` (which times on scratch copies
+    of C, so C is written once).  Returns the batch (it keeps the operands alive)."""
     count = len(A)
     batch = Batch(transa, transb, A, B, C, [alpha] * count, [beta] * count)
-    if tile is None:
-        tile = autotune(batch, handle) if beta == 0.0 else TILES[batch.esz][0]
-    run(batch, tile, handle)
+    run(batch, autotune_plan(batch, handle) if tile is None else tile, handle)
     return batch
+
+
+def _time_ms(fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _initial_tile(esz: int, size_class: int) -> int:
+    if size_class == 0:
+        return g.GFIP_GROUP_TILE_TINY
+    if size_class == 1:
+        return g.GFIP_GROUP_TILE_SMALL
+    return g.GFIP_GROUP_TILE_DEFAULT
 
 
 _tuned: dict = {}
 
 
-def autotune(batch: Batch, handle: g.Handle | None = None, reps: int = 3) -> int:
-    """Times every compiled tile shape on this batch and returns the fastest; the choice is
-    cached per :meth:`Batch.signature`.  The timed runs overwrite C (beta is applied each
-    time), so tune on scratch output buffers or restore C afterwards."""
+def autotune_plan(batch: Batch, handle: g.Handle | None = None, reps: int = 3) -> Plan:
+    """Per size bucket, the tile shape and k-split factor that make the whole batch fastest.
+
+    Starts from the largest tile that fits each bucket, unsplit, then visits the buckets in
+    order of their share of the flops and, for each, times every candidate (each tile shape;
+    with k >= 32 also 2- and 4-way splits) with the other buckets held, keeping the fastest.
+    Timings run on scratch copies of C, so the caller's C is untouched whatever beta is.  The
+    choice is cached by :meth:`Batch.signature`."""
     key = batch.signature()
     if key in _tuned:
-        return _tuned[key]
-    best, best_ms = None, float("inf")
-    for tile in TILES[batch.esz]:
-        run(batch, tile, handle)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            run(batch, tile, handle)
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        if ms < best_ms:
-            best, best_ms = tile, ms
-    _tuned[key] = best
-    return best
+        return Plan.from_buckets(batch, _tuned[key])
+    flops = {}
+    for m, n, k in batch.sizes:
+        b = bucket_of(m, n, k)
+        flops[b] = flops.get(b, 0.0) + 2.0 * m * n * k
+    choice = {b: (_initial_tile(batch.esz, b[0]), 1) for b in flops}
+    scratch = batch.with_scratch_c()
+    h = handle or g.default_handle()
+
+    def cost(ch):
+        plan = Plan.from_buckets(scratch, ch)
+        return _time_ms(lambda: run(scratch, plan, h), reps)
+
+    best_ms = cost(choice)
+    for b in sorted(flops, key=lambda b: -flops[b]):
+        splits = SPLITS if b[1] >= 1 else (1,)
+        for tile in TILES[batch.esz]:
+            for s in splits:
+                if (tile, s) == choice[b]:
+                    continue
+                trial = dict(choice)
+                trial[b] = (tile, s)
+                ms = cost(trial)
+                if ms < best_ms:
+                    best_ms, choice = ms, trial
+    _tuned[key] = choice
+    return Plan.from_buckets(batch, choice)
+
+
+def autotune(batch: Batch, handle: g.Handle | None = None, reps: int = 3):
+    """The tuned plan of the batch (see :func:`autotune_plan`)."""
+    return autotune_plan(batch, handle, reps)
 
 
 class GraphRunner:
@@ -144,17 +258,18 @@ class GraphRunner:
     The captured launches point into the handle's workspace, so the runner owns a handle of
     its own by default (a shared handle must not grow its workspace while the graph lives)."""
 
-    def __init__(self, batch: Batch, tile: int, handle: g.Handle | None = None):
+    def __init__(self, batch: Batch, tile_or_plan, handle: g.Handle | None = None):
         self.batch = batch
+        self.plan = tile_or_plan
         self.handle = handle or g.Handle()
-        run(batch, tile, self.handle)          # sizes the workspace before capture
+        run(batch, tile_or_plan, self.handle)   # sizes the workspace before capture
         torch.cuda.synchronize()
         self.stream = torch.cuda.Stream()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.stream(self.stream):
             self.handle.bind_stream(self.stream)
             with torch.cuda.graph(self.graph, stream=self.stream):
-                run(batch, tile, self.handle)
+                run(batch, tile_or_plan, self.handle)
         self.handle.bind_stream(torch.cuda.current_stream())
 
     def replay(self):

@@ -1,6 +1,7 @@
-"""Grouped GEMM (gfip_dgemm_grouped / gfip_sgemm_grouped): a batch of uneven problems in one
-launch, through the C ABI, against the oracle per problem; CUDA-graph replay; invalid
-problems skipped with a status bit."""
+"""Grouped GEMM (gfip_?gemm_grouped, gfip_?gemm_grouped_plan): a batch of uneven problems in
+one launch, through the C ABI, against the oracle per problem: every warp-tile shape, plans
+with k-splits, the tuned plan, the full 4096-problem workload; CUDA-graph replay; tuning that
+leaves C untouched; invalid problems skipped with a status bit."""
 import numpy as np
 import pytest
 
@@ -77,11 +78,76 @@ def test_batch_matches_oracle(dev, dtype):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("splits", [2, 3, 4, 8])
+def test_split_plans_match_oracle(dev, dtype, splits):
+    """Every problem split along k (the split tiles' partial sums added in order by the last
+    warp to arrive), with the tile shapes mixed across the batch."""
+    probs = make_problems(11 + splits, 160, dtype, hi=300)
+    batch, bufs = build_batch(probs, dev)
+    codes = [g.GFIP_GROUP_PLAN(q % 3, splits) for q in range(len(probs))]
+    plan = gr.Plan(batch, codes)
+    gr.run(batch, plan)
+    torch.cuda.synchronize()
+    for p, buf in zip(probs, bufs):
+        gu.assert_close(p, buf.cpu().numpy(), label=f"split {splits}")
+    assert g.default_handle().status() == 0
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+def test_split_plan_beyond_capacity_runs_unsplit(dev, dtype):
+    """A plan whose partial sums do not fit the provisioned space: the problems past the
+    capacity run unsplit and the results are still right."""
+    probs = make_problems(21, 64, dtype, lo=64, hi=200)
+    batch, bufs = build_batch(probs, dev)
+    plan = gr.Plan.uniform(batch, g.GFIP_GROUP_TILE_SMALL, 4)
+    plan.split_elems //= 3
+    gr.run(batch, plan)
+    torch.cuda.synchronize()
+    for p, buf in zip(probs, bufs):
+        gu.assert_close(p, buf.cpu().numpy(), label="capacity")
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+def test_tuning_leaves_c_untouched_whatever_beta(dev, dtype):
+    probs = make_problems(31, 120, dtype)
+    batch, bufs = build_batch(probs, dev)
+    gr._tuned.clear()
+    plan = gr.autotune_plan(batch)
+    torch.cuda.synchronize()
+    for p, buf in zip(probs, bufs):
+        assert np.array_equal(buf.cpu().numpy().view(np.uint8), p.C0.view(np.uint8))
+    assert all((c & 0xFF) in gr.TILES[np.dtype(dtype).itemsize] for c in plan.codes)
+    gr.run(batch, plan)
+    torch.cuda.synchronize()
+    for p, buf in zip(probs, bufs):
+        gu.assert_close(p, buf.cpu().numpy(), label="tuned plan")
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+def test_full_batched_workload_matches_oracle(dev, dtype):
+    """The batched workload itself: 4096 problems, m, n, k log-uniform in [4, 256], random
+    operand orders, ld = rows + {0..7}, with the tuned plan, one launch replayed from a graph."""
+    probs = make_problems(41, 4096, dtype)
+    batch, bufs = build_batch(probs, dev)
+    plan = gr.autotune_plan(batch)
+    for p, buf in zip(probs, bufs):
+        buf.copy_(torch.from_numpy(p.C0))
+    runner = gr.GraphRunner(batch, plan)
+    for p, buf in zip(probs, bufs):
+        buf.copy_(torch.from_numpy(p.C0))
+    runner.replay()
+    torch.cuda.synchronize()
+    for p, buf in zip(probs, bufs):
+        gu.assert_close(p, buf.cpu().numpy(), label="4096-problem batch")
+    assert runner.handle.status() == 0
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
 def test_graph_replay_and_autotune(dev, dtype):
     probs = make_problems(5, 200, dtype)
     batch, bufs = build_batch(probs, dev)
     tile = gr.autotune(batch)
-    assert tile in gr.TILES[np.dtype(dtype).itemsize]
+    assert isinstance(tile, gr.Plan)
     # restore C, then capture one call and replay it: same result as the oracle
     for p, buf in zip(probs, bufs):
         buf.copy_(torch.from_numpy(p.C0))
