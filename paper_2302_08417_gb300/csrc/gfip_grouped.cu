@@ -33,26 +33,26 @@ constexpr unsigned int STATUS_BAD_PROBLEM = 0x4u;  // mirrors GFIP_STATUS_BAD_PR
 
 namespace grp {
 
-constexpr int KC = 16;          // k rows per chunk
+constexpr int KC = 8;           // k rows per chunk
+constexpr int STAGES = 3;       // chunk stages per warp: two chunks in flight while one computes
 constexpr int MAX_SPLITS = 8;
 
-// Warp tile shapes (GFIP_GROUP_TILE_DEFAULT / SMALL / TINY): BM x BN per warp, TM x TN per
-// lane, lanes BM/TM along m by BN/TN along n.
+// Warp tile shapes (GFIP_GROUP_TILE_DEFAULT / SMALL / TINY), the same for both element types:
+// BM x BN per warp, TM x TN per lane, lanes BM/TM along m by BN/TN along n.  Small warp tiles
+// keep registers and shared memory per warp low, so that an SM holds many warps, each with
+// chunks in flight: these problems are bound by memory latency, not by arithmetic.
 template <typename T, int SHAPE> struct Shape;
-template <> struct Shape<float, 0> { static constexpr int BM = 64, BN = 32, TM = 8, TN = 8; };
-template <> struct Shape<float, 1> { static constexpr int BM = 32, BN = 32, TM = 8, TN = 4; };
-template <> struct Shape<float, 2> { static constexpr int BM = 16, BN = 16, TM = 4, TN = 2; };
-template <> struct Shape<double, 0> { static constexpr int BM = 32, BN = 32, TM = 8, TN = 4; };
-template <> struct Shape<double, 1> { static constexpr int BM = 32, BN = 16, TM = 8, TN = 2; };
-template <> struct Shape<double, 2> { static constexpr int BM = 16, BN = 16, TM = 4, TN = 2; };
+template <typename T> struct Shape<T, 0> { static constexpr int BM = 32, BN = 32, TM = 8, TN = 4; };
+template <typename T> struct Shape<T, 1> { static constexpr int BM = 32, BN = 16, TM = 8, TN = 2; };
+template <typename T> struct Shape<T, 2> { static constexpr int BM = 16, BN = 16, TM = 4, TN = 2; };
 
 __host__ __device__ constexpr int shape_bm(int es, int shape)
 {
-    return es == 4 ? (shape == 0 ? 64 : shape == 1 ? 32 : 16) : (shape == 2 ? 16 : 32);
+    return (void)es, shape == 2 ? 16 : 32;
 }
 __host__ __device__ constexpr int shape_bn(int es, int shape)
 {
-    return es == 4 ? (shape == 2 ? 16 : 32) : (shape == 0 ? 32 : 16);
+    return (void)es, shape == 0 ? 32 : 16;
 }
 
 // Shared-memory pitch of a chunk row: 16 bytes of padding spread the transposing copies over
@@ -62,19 +62,22 @@ template <typename T> __host__ __device__ constexpr int pitch(int bx)
     return bx + 16 / static_cast<int>(sizeof(T));
 }
 
-// Per-warp shared memory: two chunk stages of the largest shape.
+// Per-warp shared memory: STAGES chunk stages of the largest shape (32 x 32).
 template <typename T> struct WarpStage {
-    static constexpr int BMX = std::is_same<T, float>::value ? 64 : 32;
-    static constexpr int BNX = 32;
-    static constexpr int ELEMS = 2 * KC * (pitch<T>(BMX) + pitch<T>(BNX));
+    static constexpr int STAGE = KC * (pitch<T>(32) + pitch<T>(32));
+    static constexpr int ELEMS = STAGES * STAGE;
 };
 
-// CTA of independent warps; FP32: 8 warps, two CTAs per SM (16 warps, 128 registers a
-// thread); FP64: 4 warps, three CTAs per SM (12 warps, 168 registers).
+// CTA of independent warps; FP32: 12 warps, two CTAs per SM (24 warps, 80 registers a
+// thread); FP64: 8 warps, two CTAs per SM (16 warps, 128 registers).  Each CTA also keeps a
+// coarse copy of the unit prefix sums (every COARSE-th entry) for the unit look-up.
+constexpr int COARSE = 32;
+constexpr int COARSE_MAX = 512;    // entries kept in shared memory (batches up to 16384)
 template <typename T> struct Launch {
-    static constexpr int WARPS = std::is_same<T, float>::value ? 8 : 4;
-    static constexpr int MIN_BLOCKS = std::is_same<T, float>::value ? 2 : 3;
-    static constexpr size_t SMEM = (size_t)WARPS * WarpStage<T>::ELEMS * sizeof(T);
+    static constexpr int WARPS = std::is_same<T, float>::value ? 12 : 8;
+    static constexpr int MIN_BLOCKS = 2;
+    static constexpr size_t SMEM =
+        (size_t)WARPS * WarpStage<T>::ELEMS * sizeof(T) + COARSE_MAX * sizeof(int);
 };
 
 __device__ __forceinline__ bool trans_ok(char t)
@@ -175,33 +178,36 @@ __device__ void warp_tile(const GroupParams<T> &gp, const GroupDesc<T> &d, int t
         const int nch = (ke - kb + KC - 1) / KC;
         const bool acon = d.order & 1, bcon = (d.order >> 1) & 1;
         const uint32_t s0 = smem_addr(stage);
+        constexpr int ST = WarpStage<T>::STAGE;
         auto issue = [&](int c) {
-            const uint32_t sa = s0 + (uint32_t)((c & 1) * (SA + SB)) * sizeof(T);
+            const uint32_t sa = s0 + (uint32_t)((c % STAGES) * ST) * sizeof(T);
             load_chunk<T, BM>(sa, d.A, d.lda, acon, i * BM, d.m, kb + c * KC, ke, lane);
             load_chunk<T, BN>(sa + SA * sizeof(T), d.B, d.ldb, bcon, j * BN, d.n, kb + c * KC,
                               ke, lane);
-            cp_async_commit();
         };
-        issue(0);
+#pragma unroll
+        for (int c = 0; c < STAGES - 1; ++c) {
+            if (c < nch) issue(c);
+            cp_async_commit();
+        }
         for (int c = 0; c < nch; ++c) {
-            if (c + 1 < nch) {
-                issue(c + 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
+            // the stage of chunk c + STAGES - 1 held chunk c - 1, computed last iteration
+            if (c + STAGES - 1 < nch) issue(c + STAGES - 1);
+            cp_async_commit();
+            cp_async_wait<STAGES - 1>();   // chunk c has landed
             __syncwarp();
-            const T *As = stage + (c & 1) * (SA + SB);
+            const T *As = stage + (c % STAGES) * ST;
             const T *Bs = As + SA;
-#pragma unroll 4
+#pragma unroll
             for (int kk = 0; kk < KC; ++kk) {
                 T a[TM], b[TN];
                 lds_vec<T, TM>(a, As + kk * PA + lr * TM);
                 lds_vec<T, TN>(b, Bs + kk * PB + lc * TN);
                 fma_tile<T, TM, TN>(a, b, acc);
             }
-            __syncwarp();   // the stage is refilled by the next iteration's copies
+            __syncwarp();   // the stage is refilled two iterations later
         }
+        cp_async_wait<0>();
     }
 
     const int row0 = i * BM + lr * TM, col0 = j * BN + lc * TN;
@@ -304,82 +310,92 @@ template <typename T> __global__ void prepare_kernel(const GroupParams<T> gp)
     gp.pelems[r] = splits > 1 ? (int64_t)tiles * splits * bm * bn_ : 0;
 }
 
-// Exclusive prefix sum of v[0..count) over one CTA of 1024 threads (each scanning a
-// contiguous run); returns the total to every thread.  part is 1024 shared words.
-template <typename V>
-__device__ V block_scan(V *v, int count, V *part)
+// The three counts of a rank that the launch scans together.
+struct Counts {
+    int units, stiles;
+    int64_t pelems;
+    __device__ Counts operator+(const Counts &o) const
+    {
+        return Counts{units + o.units, stiles + o.stiles, pelems + o.pelems};
+    }
+};
+
+// Exclusive prefix sums of the counts of ranks 0..count-1, in place, over one CTA of 1024
+// threads (each scanning a contiguous run of ranks); returns the totals.
+template <typename T>
+__device__ Counts scan_counts(const GroupParams<T> &gp, Counts *part)
 {
+    const int count = gp.count;
     const int tid = threadIdx.x;
     const int per = (count + 1023) / 1024;
     const int lo = min(count, tid * per), hi = min(count, lo + per);
-    V sum = 0;
-    for (int q = lo; q < hi; ++q) sum += v[q];
+    Counts sum{0, 0, 0};
+    for (int q = lo; q < hi; ++q) sum = sum + Counts{gp.units[q], gp.stiles[q], gp.pelems[q]};
     part[tid] = sum;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
-        const V x = tid >= off ? part[tid - off] : V(0);
+        const Counts x = tid >= off ? part[tid - off] : Counts{0, 0, 0};
         __syncthreads();
-        part[tid] += x;
+        part[tid] = part[tid] + x;
         __syncthreads();
     }
-    V run = part[tid] - sum;
+    Counts run{part[tid].units - sum.units, part[tid].stiles - sum.stiles,
+               part[tid].pelems - sum.pelems};
     for (int q = lo; q < hi; ++q) {
-        const V c = v[q];
-        v[q] = run;
-        run += c;
+        const Counts c{gp.units[q], gp.stiles[q], gp.pelems[q]};
+        gp.units[q] = run.units;
+        gp.stiles[q] = run.stiles;
+        gp.pelems[q] = run.pelems;
+        run = run + c;
     }
-    const V total = part[1023];
+    const Counts total = part[1023];
     __syncthreads();
     return total;
 }
 
 template <typename T> __global__ void __launch_bounds__(1024) scan_kernel(const GroupParams<T> gp)
 {
-    __shared__ int64_t part[1024];
-    __shared__ int ipart[1024];
+    __shared__ Counts part[1024];
     const int count = gp.count;
     const int tid = threadIdx.x;
     constexpr int ES = static_cast<int>(sizeof(T));
-    // 1. where each split problem's partial sums and counters would start, in processing
-    //    order; a problem whose range would pass the workspace's capacity runs unsplit (a
-    //    clean cut: both prefixes only grow)
-    block_scan<int64_t>(gp.pelems, count, part);
-    block_scan<int>(gp.stiles, count, ipart);
-    for (int r = tid; r < count; r += 1024) {
-        GroupDesc<T> &d = gp.desc[gp.order ? gp.order[r] : r];
-        if (d.splits <= 1) continue;
-        const int tiles = gp.units[r] / d.splits;
-        const int64_t pe = (int64_t)tiles * d.splits * shape_bm(ES, d.shape) *
-                           shape_bn(ES, d.shape);
-        if (gp.pelems[r] + pe > gp.partial_capacity ||
-            gp.stiles[r] + tiles > gp.max_split_tiles) {
-            d.splits = 1;
-            d.ks = ((d.k + KC - 1) / KC) * KC;
-            gp.units[r] = tiles;
+    if (gp.plan != nullptr) {
+        // where each split problem's partial sums and counters would start, in processing
+        // order; a problem whose range would pass the workspace's capacity runs unsplit (a
+        // clean cut: both prefixes only grow).  units[] keeps the per-rank unit counts.
+        int *keep_units = gp.prefix;   // scratch: the unscanned unit counts
+        for (int r = tid; r < count; r += 1024) keep_units[r] = gp.units[r];
+        __syncthreads();
+        scan_counts<T>(gp, part);
+        for (int r = tid; r < count; r += 1024) {
+            GroupDesc<T> &d = gp.desc[gp.order ? gp.order[r] : r];
+            const int tiles = keep_units[r] / d.splits;
+            if (d.splits > 1) {
+                const int64_t pe = (int64_t)tiles * d.splits * shape_bm(ES, d.shape) *
+                                   shape_bn(ES, d.shape);
+                if (gp.pelems[r] + pe > gp.partial_capacity ||
+                    gp.stiles[r] + tiles > gp.max_split_tiles) {
+                    d.splits = 1;
+                    d.ks = ((d.k + KC - 1) / KC) * KC;
+                }
+            }
+            gp.units[r] = tiles * d.splits;
+            gp.stiles[r] = d.splits > 1 ? tiles : 0;
+            gp.pelems[r] = d.splits > 1 ? (int64_t)tiles * d.splits * shape_bm(ES, d.shape) *
+                                              shape_bn(ES, d.shape)
+                                        : 0;
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // 2. the final counts, then their prefix sums
-    for (int r = tid; r < count; r += 1024) {
-        const GroupDesc<T> &d = gp.desc[gp.order ? gp.order[r] : r];
-        const int tiles = gp.units[r] / d.splits;
-        gp.stiles[r] = d.splits > 1 ? tiles : 0;
-        gp.pelems[r] = d.splits > 1 ? (int64_t)tiles * d.splits * shape_bm(ES, d.shape) *
-                                          shape_bn(ES, d.shape)
-                                    : 0;
-        gp.prefix[r] = gp.units[r];
-    }
-    __syncthreads();
-    block_scan<int64_t>(gp.pelems, count, part);
-    const int stiles = block_scan<int>(gp.stiles, count, ipart);
-    const int units = block_scan<int>(gp.prefix, count, ipart);
+    const Counts total = scan_counts<T>(gp, part);
     for (int r = tid; r < count; r += 1024) {
         GroupDesc<T> &d = gp.desc[gp.order ? gp.order[r] : r];
         d.ctr_off = gp.stiles[r];
         d.part_off = gp.pelems[r];
+        gp.prefix[r] = gp.units[r];
     }
-    if (tid == 0) gp.prefix[count] = units;
-    for (int q = tid; q < stiles; q += 1024) gp.counters[q] = 0;
+    if (tid == 0) gp.prefix[count] = total.units;
+    for (int q = tid; q < total.stiles; q += 1024) gp.counters[q] = 0;
 }
 
 template <typename T>
@@ -389,12 +405,30 @@ __global__ void __launch_bounds__(Launch<T>::WARPS * 32, Launch<T>::MIN_BLOCKS)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *stage = reinterpret_cast<T *>(smem_raw) + warp * WarpStage<T>::ELEMS;
+    int *coarse = reinterpret_cast<int *>(smem_raw + (size_t)Launch<T>::WARPS *
+                                                          WarpStage<T>::ELEMS * sizeof(T));
     const int count = gp.count;
+    // every COARSE-th entry of the prefix sums, for a look-up in two short searches
+    const int ncoarse = count / COARSE + 1;
+    const bool use_coarse = ncoarse <= COARSE_MAX;
+    if (use_coarse)
+        for (int t = threadIdx.x; t < ncoarse; t += blockDim.x) coarse[t] = gp.prefix[t * COARSE];
+    __syncthreads();
     const int total = gp.prefix[count];
     const int nwarps = gridDim.x * Launch<T>::WARPS;
     for (int u = blockIdx.x * Launch<T>::WARPS + warp; u < total; u += nwarps) {
         // rank of unit u: the last r with prefix[r] <= u
         int lo = 0, hi = count - 1;
+        if (use_coarse) {
+            int clo = 0, chi = ncoarse - 1;
+            while (clo < chi) {
+                const int mid = (clo + chi + 1) >> 1;
+                if (coarse[mid] <= u) clo = mid;
+                else chi = mid - 1;
+            }
+            lo = clo * COARSE;
+            hi = min(count - 1, lo + COARSE - 1);
+        }
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (__ldg(gp.prefix + mid) <= u) lo = mid;
