@@ -198,12 +198,25 @@ __device__ void warp_tile(const GroupParams<T> &gp, const GroupDesc<T> &d, int t
             __syncwarp();
             const T *As = stage + (c % STAGES) * ST;
             const T *Bs = As + SA;
+            if (c + 1 < nch || (ke - kb) % KC == 0) {
 #pragma unroll
-            for (int kk = 0; kk < KC; ++kk) {
-                T a[TM], b[TN];
-                lds_vec<T, TM>(a, As + kk * PA + lr * TM);
-                lds_vec<T, TN>(b, Bs + kk * PB + lc * TN);
-                fma_tile<T, TM, TN>(a, b, acc);
+                for (int kk = 0; kk < KC; ++kk) {
+                    T a[TM], b[TN];
+                    lds_vec<T, TM>(a, As + kk * PA + lr * TM);
+                    lds_vec<T, TN>(b, Bs + kk * PB + lc * TN);
+                    fma_tile<T, TM, TN>(a, b, acc);
+                }
+            } else {
+                // the range's last chunk: only its rows of k that exist (the rest is zero
+                // padding, and skipping it is warp-uniform, so it saves pipe time)
+                const int kext = (ke - kb) % KC;
+#pragma unroll 1
+                for (int kk = 0; kk < kext; ++kk) {
+                    T a[TM], b[TN];
+                    lds_vec<T, TM>(a, As + kk * PA + lr * TM);
+                    lds_vec<T, TN>(b, Bs + kk * PB + lc * TN);
+                    fma_tile<T, TM, TN>(a, b, acc);
+                }
             }
             __syncwarp();   // the stage is refilled two iterations later
         }

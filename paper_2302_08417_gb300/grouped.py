@@ -197,12 +197,22 @@ def _time_ms(fn, reps):
     return statistics.median(ts)
 
 
-def _initial_tile(esz: int, size_class: int) -> int:
-    if size_class == 0:
-        return g.GFIP_GROUP_TILE_TINY
-    if size_class == 1:
-        return g.GFIP_GROUP_TILE_SMALL
-    return g.GFIP_GROUP_TILE_DEFAULT
+def padded_work(esz: int, tile: int, m: int, n: int, k: int) -> int:
+    """Multiply-adds a problem costs in a tile shape, padding of m, n and k included."""
+    bm, bn = SHAPES[(esz, tile)]
+    return math.ceil(m / bm) * bm * math.ceil(n / bn) * bn * max(k, 1)
+
+
+def _initial_tiles(batch: Batch) -> dict:
+    """Per bucket, the tile shape with the least padded work over the bucket's problems (the
+    larger tile on a tie): the start of the search, and what bounds FP64 (DFMA-bound)."""
+    work = {}
+    for m, n, k in batch.sizes:
+        b = bucket_of(m, n, k)
+        w = work.setdefault(b, {t: 0 for t in TILES[batch.esz]})
+        for t in w:
+            w[t] += padded_work(batch.esz, t, m, n, k)
+    return {b: min(sorted(w), key=lambda t: w[t]) for b, w in work.items()}
 
 
 _tuned: dict = {}
@@ -211,7 +221,7 @@ _tuned: dict = {}
 def autotune_plan(batch: Batch, handle: g.Handle | None = None, reps: int = 3) -> Plan:
     """Per size bucket, the tile shape and k-split factor that make the whole batch fastest.
 
-    Starts from the largest tile that fits each bucket, unsplit, then visits the buckets in
+    Starts from the tile with the least padded work in each bucket, unsplit, then visits the buckets in
     order of their share of the flops and, for each, times every candidate (each tile shape;
     with k >= 32 also 2- and 4-way splits) with the other buckets held, keeping the fastest.
     Timings run on scratch copies of C, so the caller's C is untouched whatever beta is.  The
@@ -223,7 +233,8 @@ def autotune_plan(batch: Batch, handle: g.Handle | None = None, reps: int = 3) -
     for m, n, k in batch.sizes:
         b = bucket_of(m, n, k)
         flops[b] = flops.get(b, 0.0) + 2.0 * m * n * k
-    choice = {b: (_initial_tile(batch.esz, b[0]), 1) for b in flops}
+    start = _initial_tiles(batch)
+    choice = {b: (start[b], 1) for b in flops}
     scratch = batch.with_scratch_c()
     h = handle or g.default_handle()
 
