@@ -267,8 +267,8 @@ int gfip_strsm(gfip_handle_t handle, char side, char uplo, char transa, char dia
  * area); the workspace must hold gfip_grouped_plan_workspace_size(count, split_elems) bytes,
  * and a problem whose partial sums would not fit runs unsplit.  The plan is chosen per size
  * bucket by the Python autotuner (grouped.autotune_plan). */
-#define GFIP_GROUP_TILE_DEFAULT 0   /* warp tile FP32 64 x 32, FP64 32 x 32                     */
-#define GFIP_GROUP_TILE_SMALL 1     /* warp tile FP32 32 x 32, FP64 32 x 16                     */
+#define GFIP_GROUP_TILE_DEFAULT 0   /* warp tile 32 x 32                                        */
+#define GFIP_GROUP_TILE_SMALL 1     /* warp tile 32 x 16                                        */
 #define GFIP_GROUP_TILE_TINY 2      /* warp tile 16 x 16                                        */
 #define GFIP_GROUP_PLAN(tile, splits) ((tile) | ((splits) << 8))
 size_t gfip_grouped_workspace_size(gfip_handle_t handle, int count);

@@ -19,11 +19,11 @@ from . import gemmfip as g
 
 TILES = {8: (g.GFIP_GROUP_TILE_DEFAULT, g.GFIP_GROUP_TILE_SMALL, g.GFIP_GROUP_TILE_TINY),
          4: (g.GFIP_GROUP_TILE_DEFAULT, g.GFIP_GROUP_TILE_SMALL, g.GFIP_GROUP_TILE_TINY)}
-# warp tile (rows x columns of C) of each tile shape, per element size
-SHAPES = {(4, 0): (64, 32), (4, 1): (32, 32), (4, 2): (16, 16),
+# warp tile (rows x columns of C) of each tile shape, per element size (as in gfip_grouped.cu)
+SHAPES = {(4, 0): (32, 32), (4, 1): (32, 16), (4, 2): (16, 16),
           (8, 0): (32, 32), (8, 1): (32, 16), (8, 2): (16, 16)}
 SPLITS = (1, 2, 4)
-KC = 16   # k rows per chunk of the warp pipeline
+KC = 8    # k rows per chunk of the warp pipeline (as in gfip_grouped.cu)
 
 
 class Batch:
