@@ -33,8 +33,29 @@ constexpr unsigned int STATUS_BAD_PROBLEM = 0x4u;  // mirrors GFIP_STATUS_BAD_PR
 
 namespace grp {
 
-constexpr int KC = 8;           // k rows per chunk
-constexpr int STAGES = 3;       // chunk stages per warp: two chunks in flight while one computes
+// Per element type: k rows per chunk (KC), chunk stages per warp (STAGES - 1 chunks in flight
+// while one computes), warps per CTA (two CTAs per SM), the fastest of a measured sweep on the
+// 4096-problem batch.  (Overridable at build time for such sweeps.)
+#ifndef GFIP_GRP_F32_KC
+#define GFIP_GRP_F32_KC 8
+#endif
+#ifndef GFIP_GRP_F32_STAGES
+#define GFIP_GRP_F32_STAGES 3
+#endif
+#ifndef GFIP_GRP_F32_WARPS
+#define GFIP_GRP_F32_WARPS 10
+#endif
+template <typename T> struct Pipe;
+template <> struct Pipe<float> {
+    static constexpr int KC = GFIP_GRP_F32_KC, STAGES = GFIP_GRP_F32_STAGES,
+                         WARPS = GFIP_GRP_F32_WARPS;
+};
+#ifndef GFIP_GRP_F64_WARPS
+#define GFIP_GRP_F64_WARPS 8
+#endif
+template <> struct Pipe<double> {
+    static constexpr int KC = 8, STAGES = 3, WARPS = GFIP_GRP_F64_WARPS;
+};
 constexpr int MAX_SPLITS = 8;
 
 // Warp tile shapes (GFIP_GROUP_TILE_DEFAULT / SMALL / TINY), the same for both element types:
@@ -64,17 +85,16 @@ template <typename T> __host__ __device__ constexpr int pitch(int bx)
 
 // Per-warp shared memory: STAGES chunk stages of the largest shape (32 x 32).
 template <typename T> struct WarpStage {
-    static constexpr int STAGE = KC * (pitch<T>(32) + pitch<T>(32));
-    static constexpr int ELEMS = STAGES * STAGE;
+    static constexpr int STAGE = Pipe<T>::KC * (pitch<T>(32) + pitch<T>(32));
+    static constexpr int ELEMS = Pipe<T>::STAGES * STAGE;
 };
 
-// CTA of independent warps; FP32: 12 warps, two CTAs per SM (24 warps, 80 registers a
-// thread); FP64: 8 warps, two CTAs per SM (16 warps, 128 registers).  Each CTA also keeps a
-// coarse copy of the unit prefix sums (every COARSE-th entry) for the unit look-up.
+// CTA of independent warps, two CTAs per SM.  Each CTA also keeps a coarse copy of the unit
+// prefix sums (every COARSE-th entry) for the unit look-up.
 constexpr int COARSE = 32;
 constexpr int COARSE_MAX = 512;    // entries kept in shared memory (batches up to 16384)
 template <typename T> struct Launch {
-    static constexpr int WARPS = std::is_same<T, float>::value ? 12 : 8;
+    static constexpr int WARPS = Pipe<T>::WARPS;
     static constexpr int MIN_BLOCKS = 2;
     static constexpr size_t SMEM =
         (size_t)WARPS * WarpStage<T>::ELEMS * sizeof(T) + COARSE_MAX * sizeof(int);
@@ -85,35 +105,75 @@ __device__ __forceinline__ bool trans_ok(char t)
     return t == 'N' || t == 'n' || t == 'T' || t == 't' || t == 'C' || t == 'c';
 }
 
-// Element copies of one k chunk (rows k0 .. k0 + KC - 1, of which kend - k0 exist) of a
-// BX-wide operand tile at x0 into the stage (row kk at kk * P); element (x, kk) of op(X)
-// sits at g[(x0+x) + (k0+kk)*ld] when contig, else at g[(k0+kk) + (x0+x)*ld].
-template <typename T, int BX>
-__device__ __forceinline__ void load_chunk(uint32_t sdst, const T *g, int64_t ld, bool contig,
-                                           int x0, int x_ext, int k0, int kend, int lane)
-{
-    constexpr int P = pitch<T>(BX);
-    constexpr int N = BX * KC / 32;
-    if (contig) {
-#pragma unroll 4
-        for (int r = 0; r < N; ++r) {
-            const int e = lane + 32 * r;
-            const int x = e % BX, kk = e / BX;
-            const bool ok = (x0 + x < x_ext) && (k0 + kk < kend);
-            const T *src = ok ? g + (int64_t)(x0 + x) + (int64_t)(k0 + kk) * ld : g;
-            cp_async_elem<sizeof(T)>(sdst + (kk * P + x) * sizeof(T), src, ok);
+// Element copies of the k chunks of one BX-wide operand tile at x0 (chunk rows kk at kk * P in
+// the stage); element (x, kk) of op(X) sits at g[x + kk*ld] when contig, else at g[kk + x*ld].
+// When contig, a warp row copies BX consecutive elements of 32 / BX k rows; otherwise KC
+// lanes copy the KC consecutive k values of one x.  Either way a lane's N elements of a chunk
+// lie rstep apart in global memory and a constant apart in the stage, and the next chunk's
+// are one chunk further on.  Elements whose x lies past the problem's edge are zero-filled
+// without a read (bit r of the mask); rows of k past the range's end only occur in its last
+// chunk (kext < KC there).  Five registers of state: the pointer, its stride, the mask.
+template <typename T, int BX> struct ChunkLoader {
+    static constexpr int KC = Pipe<T>::KC;
+    static constexpr int P = pitch<T>(BX);
+    static constexpr int N = BX * KC / 32;
+    static constexpr uint32_t CONTIG = 1u << 31;
+    static_assert(N <= 31, "one mask bit per element");
+    const T *p;
+    int64_t rstep;
+    uint32_t mask;   // bit r: element r is inside the problem; CONTIG: the layout
+
+    __device__ __forceinline__ ChunkLoader(const T *g, int64_t ld, bool contig, int x0,
+                                           int x_ext, int k0, int lane)
+    {
+        int xl, xstep;
+        if (contig) {
+            xl = lane % BX;
+            xstep = 0;
+            p = g + (x0 + xl) + (int64_t)(k0 + lane / BX) * ld;
+            rstep = (int64_t)(32 / BX) * ld;
+        } else {
+            xl = lane / KC;
+            xstep = 32 / KC;
+            p = g + (k0 + lane % KC) + (int64_t)(x0 + xl) * ld;
+            rstep = (int64_t)xstep * ld;
         }
-    } else {
-#pragma unroll 4
-        for (int r = 0; r < N; ++r) {
-            const int e = lane + 32 * r;
-            const int kk = e % KC, x = e / KC;
-            const bool ok = (x0 + x < x_ext) && (k0 + kk < kend);
-            const T *src = ok ? g + (int64_t)(k0 + kk) + (int64_t)(x0 + x) * ld : g;
-            cp_async_elem<sizeof(T)>(sdst + (kk * P + x) * sizeof(T), src, ok);
+        mask = contig ? CONTIG : 0u;
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+            if (x0 + xl + r * xstep < x_ext) mask |= 1u << r;
+    }
+
+    // Copies the next chunk (kext of its KC rows exist) into the stage at sdst; safe is any
+    // readable address, passed for the elements not read.
+    __device__ __forceinline__ void issue(uint32_t sdst, const T *safe, int kext, int lane)
+    {
+        if (mask & CONTIG) {
+            constexpr int KS = 32 / BX;
+            const int kk0 = lane / BX;
+            const uint32_t d0 = sdst + (uint32_t)(kk0 * P + lane % BX) * sizeof(T);
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+                const bool ok = ((mask >> r) & 1u) && (kk0 + r * KS < kext);
+                cp_async_elem<sizeof(T)>(d0 + (uint32_t)(r * KS * P) * sizeof(T),
+                                         ok ? p + r * rstep : safe, ok);
+            }
+            p += rstep * N;   // KC rows of k
+        } else {
+            constexpr int XS = 32 / KC;
+            const int kk0 = lane % KC;
+            const bool kok = kk0 < kext;
+            const uint32_t d0 = sdst + (uint32_t)(kk0 * P + lane / KC) * sizeof(T);
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+                const bool ok = ((mask >> r) & 1u) && kok;
+                cp_async_elem<sizeof(T)>(d0 + (uint32_t)(r * XS) * sizeof(T),
+                                         ok ? p + r * rstep : safe, ok);
+            }
+            p += KC;
         }
     }
-}
+};
 
 template <typename T, int N> __device__ __forceinline__ void lds_vec(T *d, const T *s)
 {
@@ -161,10 +221,11 @@ __device__ void warp_tile(const GroupParams<T> &gp, const GroupDesc<T> &d, int t
 {
     using S = Shape<T, SHAPE>;
     constexpr int BM = S::BM, BN = S::BN, TM = S::TM, TN = S::TN;
+    constexpr int KC = Pipe<T>::KC, STAGES = Pipe<T>::STAGES;
     constexpr int LR = BM / TM;
     static_assert(LR * (BN / TN) == 32, "a tile shape must spread over 32 lanes");
     constexpr int PA = pitch<T>(BM), PB = pitch<T>(BN);
-    constexpr int SA = KC * PA, SB = KC * PB;   // elements per stage of A and of B
+    constexpr int SA = KC * PA;   // elements of A per stage (B follows)
     const int i = tile % d.mt, j = tile / d.mt;
     const int lr = lane % LR, lc = lane / LR;
     T acc[TM][TN];
@@ -179,11 +240,13 @@ __device__ void warp_tile(const GroupParams<T> &gp, const GroupDesc<T> &d, int t
         const bool acon = d.order & 1, bcon = (d.order >> 1) & 1;
         const uint32_t s0 = smem_addr(stage);
         constexpr int ST = WarpStage<T>::STAGE;
-        auto issue = [&](int c) {
+        ChunkLoader<T, BM> la(d.A, d.lda, acon, i * BM, d.m, kb, lane);
+        ChunkLoader<T, BN> lb(d.B, d.ldb, bcon, j * BN, d.n, kb, lane);
+        auto issue = [&](int c) {   // chunks are issued in order
             const uint32_t sa = s0 + (uint32_t)((c % STAGES) * ST) * sizeof(T);
-            load_chunk<T, BM>(sa, d.A, d.lda, acon, i * BM, d.m, kb + c * KC, ke, lane);
-            load_chunk<T, BN>(sa + SA * sizeof(T), d.B, d.ldb, bcon, j * BN, d.n, kb + c * KC,
-                              ke, lane);
+            const int kext = min(KC, ke - (kb + c * KC));
+            la.issue(sa, d.A, kext, lane);
+            lb.issue(sa + SA * sizeof(T), d.B, kext, lane);
         };
 #pragma unroll
         for (int c = 0; c < STAGES - 1; ++c) {
@@ -306,6 +369,7 @@ template <typename T> __global__ void prepare_kernel(const GroupParams<T> gp)
     if (shape < 0 || shape > 2) shape = 0;
     const int es = static_cast<int>(sizeof(T));
     const int bm = shape_bm(es, shape), bn_ = shape_bn(es, shape);
+    constexpr int KC = Pipe<T>::KC;
     const int chunks = use_ab ? (k + KC - 1) / KC : 0;
     splits = max(1, min(min(splits, MAX_SPLITS), max(1, chunks)));
     d.shape = shape;
@@ -333,82 +397,99 @@ struct Counts {
     }
 };
 
-// Exclusive prefix sums of the counts of ranks 0..count-1, in place, over one CTA of 1024
-// threads (each scanning a contiguous run of ranks); returns the totals.
-template <typename T>
-__device__ Counts scan_counts(const GroupParams<T> &gp, Counts *part)
+__device__ __forceinline__ Counts shfl_up(const Counts &v, int off)
 {
-    const int count = gp.count;
-    const int tid = threadIdx.x;
-    const int per = (count + 1023) / 1024;
-    const int lo = min(count, tid * per), hi = min(count, lo + per);
-    Counts sum{0, 0, 0};
-    for (int q = lo; q < hi; ++q) sum = sum + Counts{gp.units[q], gp.stiles[q], gp.pelems[q]};
-    part[tid] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const Counts x = tid >= off ? part[tid - off] : Counts{0, 0, 0};
-        __syncthreads();
-        part[tid] = part[tid] + x;
-        __syncthreads();
-    }
-    Counts run{part[tid].units - sum.units, part[tid].stiles - sum.stiles,
-               part[tid].pelems - sum.pelems};
-    for (int q = lo; q < hi; ++q) {
-        const Counts c{gp.units[q], gp.stiles[q], gp.pelems[q]};
-        gp.units[q] = run.units;
-        gp.stiles[q] = run.stiles;
-        gp.pelems[q] = run.pelems;
-        run = run + c;
-    }
-    const Counts total = part[1023];
-    __syncthreads();
-    return total;
+    return Counts{__shfl_up_sync(0xffffffffu, v.units, off),
+                  __shfl_up_sync(0xffffffffu, v.stiles, off),
+                  static_cast<int64_t>(__shfl_up_sync(
+                      0xffffffffu, static_cast<long long>(v.pelems), off))};
 }
 
+__device__ __forceinline__ Counts warp_inclusive(Counts v, int lane)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const Counts x = shfl_up(v, off);
+        if (lane >= off) v = v + x;
+    }
+    return v;
+}
+
+// Exclusive prefix of v over the 1024 threads of the CTA (thread order); *total gets the sum.
+// wsum is 33 entries of shared memory, free again when the call returns.
+__device__ Counts block_exclusive(const Counts &v, Counts *wsum, Counts *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Counts inc = warp_inclusive(v, lane);
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const Counts w = wsum[lane];
+        const Counts winc = warp_inclusive(w, lane);
+        wsum[lane] = Counts{winc.units - w.units, winc.stiles - w.stiles, winc.pelems - w.pelems};
+        if (lane == 31) wsum[32] = winc;
+    }
+    __syncthreads();
+    const Counts base = wsum[warp];
+    *total = wsum[32];
+    __syncthreads();
+    return Counts{base.units + inc.units - v.units, base.stiles + inc.stiles - v.stiles,
+                  base.pelems + inc.pelems - v.pelems};
+}
+
+// One CTA of 1024 threads turns the per-rank counts into the unit prefix sums the GEMM
+// kernel searches and gives each split problem its arrival counters and partial-sum space,
+// 1024 ranks at a time (coalesced loads, warp-shuffle scans).  With a plan, a split problem
+// whose space would pass the workspace's capacity runs unsplit instead: the requested space
+// before a rank only grows with the rank, so the kept problems are exactly those before the
+// first cut and their places do not move.
 template <typename T> __global__ void __launch_bounds__(1024) scan_kernel(const GroupParams<T> gp)
 {
-    __shared__ Counts part[1024];
+    __shared__ Counts wsum[33];
     const int count = gp.count;
     const int tid = threadIdx.x;
-    constexpr int ES = static_cast<int>(sizeof(T));
-    if (gp.plan != nullptr) {
-        // where each split problem's partial sums and counters would start, in processing
-        // order; a problem whose range would pass the workspace's capacity runs unsplit (a
-        // clean cut: both prefixes only grow).  units[] keeps the per-rank unit counts.
-        int *keep_units = gp.prefix;   // scratch: the unscanned unit counts
-        for (int r = tid; r < count; r += 1024) keep_units[r] = gp.units[r];
-        __syncthreads();
-        scan_counts<T>(gp, part);
-        for (int r = tid; r < count; r += 1024) {
-            GroupDesc<T> &d = gp.desc[gp.order ? gp.order[r] : r];
-            const int tiles = keep_units[r] / d.splits;
-            if (d.splits > 1) {
-                const int64_t pe = (int64_t)tiles * d.splits * shape_bm(ES, d.shape) *
-                                   shape_bn(ES, d.shape);
-                if (gp.pelems[r] + pe > gp.partial_capacity ||
-                    gp.stiles[r] + tiles > gp.max_split_tiles) {
-                    d.splits = 1;
-                    d.ks = ((d.k + KC - 1) / KC) * KC;
-                }
-            }
-            gp.units[r] = tiles * d.splits;
-            gp.stiles[r] = d.splits > 1 ? tiles : 0;
-            gp.pelems[r] = d.splits > 1 ? (int64_t)tiles * d.splits * shape_bm(ES, d.shape) *
-                                              shape_bn(ES, d.shape)
-                                        : 0;
+    constexpr int KC = Pipe<T>::KC;
+    Counts carry{0, 0, 0}, req_carry{0, 0, 0};
+    // the next 1024 ranks' counts and problem indices load while these are scanned
+    Counts next{0, 0, 0};
+    int next_g = tid;
+    if (tid < count) {
+        next = Counts{gp.units[tid], gp.stiles[tid], gp.pelems[tid]};
+        if (gp.order) next_g = gp.order[tid];
+    }
+    for (int base = 0; base < count; base += 1024) {
+        const int r = base + tid;
+        Counts v = next;
+        const int g = next_g;
+        if (r + 1024 < count) {
+            next = Counts{gp.units[r + 1024], gp.stiles[r + 1024], gp.pelems[r + 1024]};
+            next_g = gp.order ? gp.order[r + 1024] : r + 1024;
         }
-        __syncthreads();
+        if (gp.plan != nullptr) {
+            Counts tot;
+            const Counts before = block_exclusive(v, wsum, &tot) + req_carry;
+            req_carry = req_carry + tot;
+            if (r < count && v.stiles > 0 &&
+                (before.pelems + v.pelems > gp.partial_capacity ||
+                 before.stiles + v.stiles > gp.max_split_tiles)) {
+                GroupDesc<T> &d = gp.desc[g];
+                d.splits = 1;
+                d.ks = ((d.k + KC - 1) / KC) * KC;
+                v = Counts{v.stiles, 0, 0};   // its tiles, unsplit
+            }
+        }
+        Counts tot;
+        const Counts before = block_exclusive(v, wsum, &tot) + carry;
+        carry = carry + tot;
+        if (r < count) {
+            GroupDesc<T> &d = gp.desc[g];
+            d.ctr_off = before.stiles;
+            d.part_off = before.pelems;
+            gp.prefix[r] = before.units;
+        }
     }
-    const Counts total = scan_counts<T>(gp, part);
-    for (int r = tid; r < count; r += 1024) {
-        GroupDesc<T> &d = gp.desc[gp.order ? gp.order[r] : r];
-        d.ctr_off = gp.stiles[r];
-        d.part_off = gp.pelems[r];
-        gp.prefix[r] = gp.units[r];
-    }
-    if (tid == 0) gp.prefix[count] = total.units;
-    for (int q = tid; q < total.stiles; q += 1024) gp.counters[q] = 0;
+    if (tid == 0) gp.prefix[count] = carry.units;
+    for (int q = tid; q < carry.stiles; q += 1024) gp.counters[q] = 0;
 }
 
 template <typename T>
@@ -429,7 +510,13 @@ __global__ void __launch_bounds__(Launch<T>::WARPS * 32, Launch<T>::MIN_BLOCKS)
     __syncthreads();
     const int total = gp.prefix[count];
     const int nwarps = gridDim.x * Launch<T>::WARPS;
-    for (int u = blockIdx.x * Launch<T>::WARPS + warp; u < total; u += nwarps) {
+    const int w = blockIdx.x * Launch<T>::WARPS + warp;
+    // units are dealt in bands of nwarps, alternately forwards and backwards (the processing
+    // order puts the costliest units first, so every warp gets a similar sum)
+    for (int band = 0;; ++band) {
+        const int u = band * nwarps + ((band & 1) ? nwarps - 1 - w : w);
+        if (band * nwarps >= total) break;
+        if (u >= total) continue;
         // rank of unit u: the last r with prefix[r] <= u
         int lo = 0, hi = count - 1;
         if (use_coarse) {

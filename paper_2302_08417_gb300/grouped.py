@@ -76,10 +76,24 @@ class Batch:
         self.lda = torch.tensor([ld(x) for x in A], **i64)
         self.ldb = torch.tensor([ld(x) for x in B], **i64)
         self.ldc = torch.tensor([ld(x) for x in C], **i64)
-        # processing order: largest problems first, so the persistent warps end together
-        rank = sorted(range(count), key=lambda q: -ms[q] * ns[q] * max(ks[q], 1))
-        self.order = torch.tensor(rank, **i32)
+        self._orders = {}
         self._keep = (A, B, C)   # the operands must outlive the batch
+
+    def order_for(self, codes) -> torch.Tensor:
+        """Processing order for per-problem plan codes: costliest work units first (see
+        :func:`unit_cost`), so that the kernel's warps, dealt the units in alternating bands,
+        end together."""
+        key = tuple(codes)
+        if key not in self._orders:
+            cost = [unit_cost(self.esz, c & 0xFF, c >> 8, *s) for s, c in zip(self.sizes, codes)]
+            rank = sorted(range(self.count), key=lambda q: (-cost[q], q))
+            self._orders[key] = torch.tensor(rank, dtype=torch.int32, device=self.device)
+        return self._orders[key]
+
+    @property
+    def order(self) -> torch.Tensor:
+        """The processing order for the default tile shape, unsplit."""
+        return self.order_for([g.GFIP_GROUP_PLAN(g.GFIP_GROUP_TILE_DEFAULT, 1)] * self.count)
 
     def flops(self) -> float:
         return sum(2.0 * m * n * k for m, n, k in self.sizes)
@@ -114,12 +128,23 @@ def bucket_of(m: int, n: int, k: int):
     return (sc, kc)
 
 
+def unit_cost(esz: int, tile: int, splits: int, m: int, n: int, k: int) -> int:
+    """Relative time of one work unit (one k-range of one warp tile) of a problem: the padded
+    multiply-adds of its k chunks, a copy overhead per chunk and an overhead per unit (look-up,
+    epilogue).  Only the order of the costs matters."""
+    bm, bn = SHAPES[(esz, tile)]
+    chunks = math.ceil(math.ceil(max(k, 1) / KC) / max(1, splits))
+    return chunks * (bm * bn + 512) + 2 * bm * bn + 2048
+
+
 class Plan:
-    """Warp-tile shape and k-split factor per problem, as the device array the library reads."""
+    """Warp-tile shape and k-split factor per problem, as the device array the library reads,
+    with the processing order that suits it."""
 
     def __init__(self, batch: Batch, codes):
         self.codes = list(codes)
         self.tensor = torch.tensor(self.codes, dtype=torch.int32, device=batch.device)
+        self.order = batch.order_for(self.codes)
         self.split_elems = 0
         for (m, n, k), c in zip(batch.sizes, self.codes):
             tile, splits = c & 0xFF, c >> 8
@@ -158,7 +183,7 @@ def run(batch: Batch, tile_or_plan, handle: g.Handle | None = None) -> None:
             batch.m.data_ptr(), batch.n.data_ptr(), batch.k.data_ptr(), batch.alpha.data_ptr(),
             batch.A.data_ptr(), batch.lda.data_ptr(), batch.B.data_ptr(), batch.ldb.data_ptr(),
             batch.beta.data_ptr(), batch.C.data_ptr(), batch.ldc.data_ptr(),
-            plan.tensor.data_ptr(), batch.order.data_ptr(), plan.split_elems)
+            plan.tensor.data_ptr(), plan.order.data_ptr(), plan.split_elems)
     else:
         _ensure(h, g.gfip_grouped_workspace_size(h.h, batch.count))
         rc = g.gfip_gemm_grouped(batch.esz, h.h, batch.count, batch.transa.data_ptr(),
