@@ -270,6 +270,8 @@ int gfip_strsm(gfip_handle_t handle, char side, char uplo, char transa, char dia
 #define GFIP_GROUP_TILE_DEFAULT 0   /* warp tile 32 x 32                                        */
 #define GFIP_GROUP_TILE_SMALL 1     /* warp tile 32 x 16                                        */
 #define GFIP_GROUP_TILE_TINY 2      /* warp tile 16 x 16                                        */
+#define GFIP_GROUP_TILE_16X8 3      /* warp tile 16 x 8                                         */
+#define GFIP_GROUP_TILE_8X16 4      /* warp tile 8 x 16                                         */
 #define GFIP_GROUP_PLAN(tile, splits) ((tile) | ((splits) << 8))
 size_t gfip_grouped_workspace_size(gfip_handle_t handle, int count);
 size_t gfip_grouped_plan_workspace_size(gfip_handle_t handle, int count, int64_t split_elems,

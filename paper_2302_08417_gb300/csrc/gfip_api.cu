@@ -1102,7 +1102,7 @@ int grouped_entry(gfip_handle_t handle, int count, const char *transa, const cha
 {
     Handle *h = get(handle);
     if (h == nullptr) return GFIP_ERR_HANDLE;
-    if (count < 0 || tile < GFIP_GROUP_TILE_DEFAULT || tile > GFIP_GROUP_TILE_TINY ||
+    if (count < 0 || tile < GFIP_GROUP_TILE_DEFAULT || tile > GFIP_GROUP_TILE_8X16 ||
         split_elems < 0)
         return GFIP_ERR_ARG;
     h->last_launches = 0;

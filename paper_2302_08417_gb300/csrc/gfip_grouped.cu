@@ -21,6 +21,7 @@
 //            unsplit), and clears the arrival counters
 //   grouped  persistent warps stride over the global unit list, largest problems first when
 //            the caller orders them so
+#include <climits>
 #include <cstdint>
 #include <type_traits>
 
@@ -58,22 +59,26 @@ template <> struct Pipe<double> {
 };
 constexpr int MAX_SPLITS = 8;
 
-// Warp tile shapes (GFIP_GROUP_TILE_DEFAULT / SMALL / TINY), the same for both element types:
-// BM x BN per warp, TM x TN per lane, lanes BM/TM along m by BN/TN along n.  Small warp tiles
-// keep registers and shared memory per warp low, so that an SM holds many warps, each with
-// chunks in flight: these problems are bound by memory latency, not by arithmetic.
+// Warp tile shapes (GFIP_GROUP_TILE_*), the same for both element types: BM x BN per warp,
+// TM x TN per lane, lanes BM/TM along m by BN/TN along n.  Small warp tiles keep registers and
+// shared memory per warp low, so that an SM holds many warps, each with chunks in flight; the
+// smallest ones cut the padding of tiny problems, which matters where the arithmetic pipe
+// bounds the batch (FP64).
 template <typename T, int SHAPE> struct Shape;
 template <typename T> struct Shape<T, 0> { static constexpr int BM = 32, BN = 32, TM = 8, TN = 4; };
 template <typename T> struct Shape<T, 1> { static constexpr int BM = 32, BN = 16, TM = 8, TN = 2; };
 template <typename T> struct Shape<T, 2> { static constexpr int BM = 16, BN = 16, TM = 4, TN = 2; };
+template <typename T> struct Shape<T, 3> { static constexpr int BM = 16, BN = 8, TM = 2, TN = 2; };
+template <typename T> struct Shape<T, 4> { static constexpr int BM = 8, BN = 16, TM = 2, TN = 2; };
+constexpr int NUM_SHAPES = 5;
 
 __host__ __device__ constexpr int shape_bm(int es, int shape)
 {
-    return (void)es, shape == 2 ? 16 : 32;
+    return (void)es, shape <= 1 ? 32 : shape <= 3 ? 16 : 8;
 }
 __host__ __device__ constexpr int shape_bn(int es, int shape)
 {
-    return (void)es, shape == 0 ? 32 : 16;
+    return (void)es, shape == 0 ? 32 : shape == 3 ? 8 : 16;
 }
 
 // Shared-memory pitch of a chunk row: 16 bytes of padding spread the transposing copies over
@@ -91,7 +96,7 @@ template <typename T> struct WarpStage {
 
 // CTA of independent warps, two CTAs per SM.  Each CTA also keeps a coarse copy of the unit
 // prefix sums (every COARSE-th entry) for the unit look-up.
-constexpr int COARSE = 32;
+constexpr int COARSE = 32;       // a warp reads the entries between two coarse ones at once
 constexpr int COARSE_MAX = 512;    // entries kept in shared memory (batches up to 16384)
 template <typename T> struct Launch {
     static constexpr int WARPS = Pipe<T>::WARPS;
@@ -175,6 +180,11 @@ template <typename T, int BX> struct ChunkLoader {
     }
 };
 
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+
 template <typename T, int N> __device__ __forceinline__ void lds_vec(T *d, const T *s)
 {
     static_assert((N * sizeof(T)) % 8 == 0, "fragments are whole 8-byte words");
@@ -234,6 +244,17 @@ __device__ void warp_tile(const GroupParams<T> &gp, const GroupDesc<T> &d, int t
 #pragma unroll
         for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = T(0);
 
+    if (d.beta != T(0) && lane < BN && j * BN + lane < d.n) {
+        // the epilogue reads this tile of C: bring its columns into L2 while the k loop runs
+        const T *c0 = d.C + (int64_t)(j * BN + lane) * d.ldc + i * BM;
+        const int rows = min(BM, d.m - i * BM);
+        constexpr int LINE = 128 / static_cast<int>(sizeof(T));
+#pragma unroll
+        for (int r = 0; r < BM; r += LINE)
+            if (r < rows) prefetch_l2(c0 + r);
+        prefetch_l2(c0 + rows - 1);
+    }
+
     if (d.ks > 0) {
         const int kb = s * d.ks, ke = min(d.k, kb + d.ks);
         const int nch = (ke - kb + KC - 1) / KC;
@@ -286,16 +307,16 @@ __device__ void warp_tile(const GroupParams<T> &gp, const GroupDesc<T> &d, int t
         cp_async_wait<0>();
     }
 
-    const int row0 = i * BM + lr * TM, col0 = j * BN + lc * TN;
     if (d.splits > 1) {
-        // store this k-range's partial sums; the last of the tile's splits to arrive adds
+        // store this k-range's partial sums (accumulator by accumulator, lanes adjacent, so
+        // that every warp access is one run); the last of the tile's splits to arrive adds
         // them all in k-range order and finishes the tile
         T *part = gp.partial + d.part_off;
-        T *mine = part + ((int64_t)tile * d.splits + s) * (BM * BN) + lane * (TM * TN);
+        T *mine = part + ((int64_t)tile * d.splits + s) * (BM * BN) + lane;
 #pragma unroll
         for (int ii = 0; ii < TM; ++ii)
 #pragma unroll
-            for (int jj = 0; jj < TN; ++jj) __stcg(mine + ii * TN + jj, acc[ii][jj]);
+            for (int jj = 0; jj < TN; ++jj) __stcg(mine + (ii * TN + jj) * 32, acc[ii][jj]);
         __threadfence();
         __syncwarp();
         int last = 0;
@@ -304,34 +325,58 @@ __device__ void warp_tile(const GroupParams<T> &gp, const GroupDesc<T> &d, int t
         if (!last) return;
         __threadfence();
         for (int t = 0; t < d.splits; ++t) {
-            const T *src = part + ((int64_t)tile * d.splits + t) * (BM * BN) + lane * (TM * TN);
+            const T *src = part + ((int64_t)tile * d.splits + t) * (BM * BN) + lane;
 #pragma unroll
             for (int ii = 0; ii < TM; ++ii)
 #pragma unroll
                 for (int jj = 0; jj < TN; ++jj) {
-                    const T v = __ldcg(src + ii * TN + jj);
+                    const T v = __ldcg(src + (ii * TN + jj) * 32);
                     acc[ii][jj] = (t == 0) ? v : acc[ii][jj] + v;
                 }
         }
     }
+    // The epilogue goes through the warp's stage (free now: every chunk has landed and been
+    // used): C's tile is copied in with lanes along its rows, whole columns at a time (every
+    // warp access one or two runs of consecutive elements, all in flight together), updated
+    // there by each lane from its accumulators, and written back the way it came in.
+    constexpr int CPITCH = BM + 1;
+    constexpr int CPI = 32 / BM;   // columns per warp access
+    constexpr int NC = BN / CPI;   // accesses per lane
+    static_assert(BN * CPITCH <= WarpStage<T>::ELEMS, "the C tile fits the warp's stage");
     const bool read_c = d.beta != T(0);
+    const int rr = lane % BM, cj = lane / BM;
+    const int row = i * BM + rr;
+    const bool row_ok = row < d.m;
+    T *crow = d.C + row;
+    if (read_c) {
+        const uint32_t st0 = smem_addr(stage);
 #pragma unroll
-    for (int jj = 0; jj < TN; ++jj) {
-        const int col = col0 + jj;
-        if (col >= d.n) continue;
-        T *ccol = d.C + (int64_t)col * d.ldc;
-        T c[TM];
-#pragma unroll
-        for (int ii = 0; ii < TM; ++ii)
-            c[ii] = (read_c && row0 + ii < d.m) ? ccol[row0 + ii] : T(0);
-#pragma unroll
-        for (int ii = 0; ii < TM; ++ii) {
-            if (row0 + ii >= d.m) continue;
-            T v = d.alpha * acc[ii][jj];
-            if (read_c) v = fma(d.beta, c[ii], v);
-            ccol[row0 + ii] = v;
+        for (int q = 0; q < NC; ++q) {
+            const int c = q * CPI + cj, col = j * BN + c;
+            const bool ok = row_ok && col < d.n;
+            cp_async_elem<sizeof(T)>(st0 + (uint32_t)(c * CPITCH + rr) * sizeof(T),
+                                     ok ? crow + (int64_t)col * d.ldc : d.C, ok);
         }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
     }
+#pragma unroll
+    for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) {
+            T &e = stage[(lc * TN + jj) * CPITCH + lr * TM + ii];
+            T v = d.alpha * acc[ii][jj];
+            if (read_c) v = fma(d.beta, e, v);
+            e = v;
+        }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const int c = q * CPI + cj, col = j * BN + c;
+        if (row_ok && col < d.n) crow[(int64_t)col * d.ldc] = stage[c * CPITCH + rr];
+    }
+    __syncwarp();   // the stage is refilled by the next unit
 }
 
 template <typename T> __global__ void prepare_kernel(const GroupParams<T> gp)
@@ -366,7 +411,7 @@ template <typename T> __global__ void prepare_kernel(const GroupParams<T> gp)
     if (bad) atomicOr(gp.status, STATUS_BAD_PROBLEM);
     const int code = gp.plan ? gp.plan[g] : gp.uniform_shape;
     int shape = code & 0xff, splits = (code >> 8) & 0xff;
-    if (shape < 0 || shape > 2) shape = 0;
+    if (shape < 0 || shape >= NUM_SHAPES) shape = 0;
     const int es = static_cast<int>(sizeof(T));
     const int bm = shape_bm(es, shape), bn_ = shape_bn(es, shape);
     constexpr int KC = Pipe<T>::KC;
@@ -380,7 +425,7 @@ template <typename T> __global__ void prepare_kernel(const GroupParams<T> gp)
     if (use_ab) d.splits = splits = (chunks + d.ks / KC - 1) / (d.ks / KC);   // no empty split
     d.ctr_off = 0;
     d.part_off = 0;
-    gp.desc[g] = d;
+    gp.desc[r] = d;
     const int tiles = nothing ? 0 : d.mt * d.nt;
     gp.units[r] = tiles * splits;
     gp.stiles[r] = splits > 1 ? tiles : 0;
@@ -450,21 +495,14 @@ template <typename T> __global__ void __launch_bounds__(1024) scan_kernel(const 
     const int tid = threadIdx.x;
     constexpr int KC = Pipe<T>::KC;
     Counts carry{0, 0, 0}, req_carry{0, 0, 0};
-    // the next 1024 ranks' counts and problem indices load while these are scanned
+    // the next 1024 ranks' counts load while these are scanned
     Counts next{0, 0, 0};
-    int next_g = tid;
-    if (tid < count) {
-        next = Counts{gp.units[tid], gp.stiles[tid], gp.pelems[tid]};
-        if (gp.order) next_g = gp.order[tid];
-    }
+    if (tid < count) next = Counts{gp.units[tid], gp.stiles[tid], gp.pelems[tid]};
     for (int base = 0; base < count; base += 1024) {
         const int r = base + tid;
         Counts v = next;
-        const int g = next_g;
-        if (r + 1024 < count) {
+        if (r + 1024 < count)
             next = Counts{gp.units[r + 1024], gp.stiles[r + 1024], gp.pelems[r + 1024]};
-            next_g = gp.order ? gp.order[r + 1024] : r + 1024;
-        }
         if (gp.plan != nullptr) {
             Counts tot;
             const Counts before = block_exclusive(v, wsum, &tot) + req_carry;
@@ -472,7 +510,7 @@ template <typename T> __global__ void __launch_bounds__(1024) scan_kernel(const 
             if (r < count && v.stiles > 0 &&
                 (before.pelems + v.pelems > gp.partial_capacity ||
                  before.stiles + v.stiles > gp.max_split_tiles)) {
-                GroupDesc<T> &d = gp.desc[g];
+                GroupDesc<T> &d = gp.desc[r];
                 d.splits = 1;
                 d.ks = ((d.k + KC - 1) / KC) * KC;
                 v = Counts{v.stiles, 0, 0};   // its tiles, unsplit
@@ -482,7 +520,7 @@ template <typename T> __global__ void __launch_bounds__(1024) scan_kernel(const 
         const Counts before = block_exclusive(v, wsum, &tot) + carry;
         carry = carry + tot;
         if (r < count) {
-            GroupDesc<T> &d = gp.desc[g];
+            GroupDesc<T> &d = gp.desc[r];
             d.ctr_off = before.stiles;
             d.part_off = before.pelems;
             gp.prefix[r] = before.units;
@@ -517,8 +555,9 @@ __global__ void __launch_bounds__(Launch<T>::WARPS * 32, Launch<T>::MIN_BLOCKS)
         const int u = band * nwarps + ((band & 1) ? nwarps - 1 - w : w);
         if (band * nwarps >= total) break;
         if (u >= total) continue;
-        // rank of unit u: the last r with prefix[r] <= u
-        int lo = 0, hi = count - 1;
+        // rank of unit u: the last r with prefix[r] <= u (ranks without units share their
+        // successor's prefix, so the last is the one that has the unit)
+        int lo, first;
         if (use_coarse) {
             int clo = 0, chi = ncoarse - 1;
             while (clo < chi) {
@@ -526,22 +565,32 @@ __global__ void __launch_bounds__(Launch<T>::WARPS * 32, Launch<T>::MIN_BLOCKS)
                 if (coarse[mid] <= u) clo = mid;
                 else chi = mid - 1;
             }
-            lo = clo * COARSE;
-            hi = min(count - 1, lo + COARSE - 1);
+            // one warp-wide read of the COARSE (= 32) entries that follow
+            const int r = clo * COARSE + lane;
+            const int pr = r < count ? __ldg(gp.prefix + r) : INT_MAX;
+            const unsigned le = __ballot_sync(0xffffffffu, pr <= u);
+            const int last = 31 - __clz(le);
+            lo = clo * COARSE + last;
+            first = __shfl_sync(0xffffffffu, pr, last);
+        } else {
+            int a = 0, b = count - 1;
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (__ldg(gp.prefix + mid) <= u) a = mid;
+                else b = mid - 1;
+            }
+            lo = a;
+            first = __ldg(gp.prefix + lo);
         }
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(gp.prefix + mid) <= u) lo = mid;
-            else hi = mid - 1;
-        }
-        const int g = gp.order ? __ldg(gp.order + lo) : lo;
-        const GroupDesc<T> d = gp.desc[g];
-        const int local = u - __ldg(gp.prefix + lo);
+        const GroupDesc<T> d = gp.desc[lo];
+        const int local = u - first;
         const int tile = local / d.splits, s = local % d.splits;
         switch (d.shape) {
         case 0: warp_tile<T, 0>(gp, d, tile, s, stage, lane); break;
         case 1: warp_tile<T, 1>(gp, d, tile, s, stage, lane); break;
-        default: warp_tile<T, 2>(gp, d, tile, s, stage, lane); break;
+        case 2: warp_tile<T, 2>(gp, d, tile, s, stage, lane); break;
+        case 3: warp_tile<T, 3>(gp, d, tile, s, stage, lane); break;
+        default: warp_tile<T, 4>(gp, d, tile, s, stage, lane); break;
         }
         __syncwarp();
     }

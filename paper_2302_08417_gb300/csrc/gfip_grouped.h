@@ -36,7 +36,7 @@ template <typename T> struct GroupParams {
     const int *plan;      // [count] shape | splits << 8 per problem, or null (uniform)
     const int *order;     // [count] processing order (problem index per rank), or null
     int uniform_shape;    // the shape of every problem when plan is null
-    GroupDesc<T> *desc;   // [count], by problem index
+    GroupDesc<T> *desc;   // [count], by rank (processing order)
     int *units;           // [count] work units (tiles x splits) per rank
     int *stiles;          // [count] split tiles per rank
     int64_t *pelems;      // [count] partial-sum elements per rank

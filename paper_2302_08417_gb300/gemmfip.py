@@ -34,6 +34,7 @@ GFIP_STATUS_MMA_TIMEOUT = 0x2
 GFIP_STATUS_BAD_PROBLEM = 0x4
 GFIP_STATUS_WAIT_TIMEOUT = 0x8
 GFIP_GROUP_TILE_DEFAULT, GFIP_GROUP_TILE_SMALL, GFIP_GROUP_TILE_TINY = 0, 1, 2
+GFIP_GROUP_TILE_16X8, GFIP_GROUP_TILE_8X16 = 3, 4
 
 
 def GFIP_GROUP_PLAN(tile: int, splits: int) -> int:

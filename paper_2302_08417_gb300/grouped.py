@@ -17,11 +17,12 @@ import torch
 
 from . import gemmfip as g
 
-TILES = {8: (g.GFIP_GROUP_TILE_DEFAULT, g.GFIP_GROUP_TILE_SMALL, g.GFIP_GROUP_TILE_TINY),
-         4: (g.GFIP_GROUP_TILE_DEFAULT, g.GFIP_GROUP_TILE_SMALL, g.GFIP_GROUP_TILE_TINY)}
+_ALL = (g.GFIP_GROUP_TILE_DEFAULT, g.GFIP_GROUP_TILE_SMALL, g.GFIP_GROUP_TILE_TINY,
+        g.GFIP_GROUP_TILE_16X8, g.GFIP_GROUP_TILE_8X16)
+TILES = {8: _ALL, 4: _ALL}
 # warp tile (rows x columns of C) of each tile shape, per element size (as in gfip_grouped.cu)
-SHAPES = {(4, 0): (32, 32), (4, 1): (32, 16), (4, 2): (16, 16),
-          (8, 0): (32, 32), (8, 1): (32, 16), (8, 2): (16, 16)}
+SHAPES = {(e, t): s for e in (4, 8)
+          for t, s in zip(_ALL, ((32, 32), (32, 16), (16, 16), (16, 8), (8, 16)))}
 SPLITS = (1, 2, 4)
 KC = 8    # k rows per chunk of the warp pipeline (as in gfip_grouped.cu)
 
@@ -246,7 +247,8 @@ _tuned: dict = {}
 def autotune_plan(batch: Batch, handle: g.Handle | None = None, reps: int = 3) -> Plan:
     """Per size bucket, the tile shape and k-split factor that make the whole batch fastest.
 
-    Starts from the tile with the least padded work in each bucket, unsplit, then visits the buckets in
+    Starts from the fastest of two kinds of plan, unsplit: the tile with the least padded work
+    in each bucket, or one tile shape for every problem.  Then visits the buckets in
     order of their share of the flops and, for each, times every candidate (each tile shape;
     with k >= 32 also 2- and 4-way splits) with the other buckets held, keeping the fastest.
     Timings run on scratch copies of C, so the caller's C is untouched whatever beta is.  The
@@ -259,7 +261,6 @@ def autotune_plan(batch: Batch, handle: g.Handle | None = None, reps: int = 3) -
         b = bucket_of(m, n, k)
         flops[b] = flops.get(b, 0.0) + 2.0 * m * n * k
     start = _initial_tiles(batch)
-    choice = {b: (start[b], 1) for b in flops}
     scratch = batch.with_scratch_c()
     h = handle or g.default_handle()
 
@@ -267,7 +268,11 @@ def autotune_plan(batch: Batch, handle: g.Handle | None = None, reps: int = 3) -
         plan = Plan.from_buckets(scratch, ch)
         return _time_ms(lambda: run(scratch, plan, h), reps)
 
-    best_ms = cost(choice)
+    # start from the fastest of: the least padded tile per bucket, or one tile everywhere
+    starts = [{b: (start[b], 1) for b in flops}]
+    starts += [{b: (t, 1) for b in flops} for t in TILES[batch.esz]]
+    best_ms, choice = min(((cost(ch), i) for i, ch in enumerate(starts)))
+    choice = starts[choice]
     for b in sorted(flops, key=lambda b: -flops[b]):
         splits = SPLITS if b[1] >= 1 else (1,)
         for tile in TILES[batch.esz]:

@@ -84,7 +84,7 @@ def test_split_plans_match_oracle(dev, dtype, splits):
     warp to arrive), with the tile shapes mixed across the batch."""
     probs = make_problems(11 + splits, 160, dtype, hi=300)
     batch, bufs = build_batch(probs, dev)
-    codes = [g.GFIP_GROUP_PLAN(q % 3, splits) for q in range(len(probs))]
+    codes = [g.GFIP_GROUP_PLAN(q % 5, splits) for q in range(len(probs))]
     plan = gr.Plan(batch, codes)
     gr.run(batch, plan)
     torch.cuda.synchronize()
