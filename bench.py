@@ -798,10 +798,10 @@ def trsm_report(g, torch, shapes=((8192, 8192), (2048, 2048))):
     """TRSM (side L, lower, 'N', non-unit, ld = m + 7; a well-conditioned system: off-diagonal
     entries U[-1, 1] / m, diagonal 2) on the fused kernel: GFLOP/s counted as m^2 n (the
     substitution's multiply-adds), fused and raw-only, against the full GEMM of the same
-    shape.  Device time of one whole solve (a diagonal solve and a GEMM update per 64-wide
-    block), CUDA events, best of a few."""
+    shape.  Device time of one whole solve (a panel solve and a GEMM update per 512-wide
+    panel), CUDA events, best of a few."""
     out = {"note": "side L, uplo L, trans N, diag N, ld = m + 7; flops m^2 n; panels of 512 "
-                   "unknowns, blocks of 64"}
+                   "unknowns, each solved in one launch, then one GEMM update"}
     h = g.Handle()
     h.bind_stream()
     for dtype, tag in ((torch.float64, "f64"), (torch.float32, "f32")):

@@ -26,7 +26,6 @@ constexpr size_t kDoneCountOffset = 128;    // header word: finished CTAs of the
 constexpr size_t kPackCountOffset = 192;    // header word: tiles packed by shared packing
 constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
 constexpr int kMinSplitRun = 8;              // shortest k run per CTA in a split wave
-constexpr int kTrsmPanel = 512;              // TRSM: unknowns per panel (two-level blocking)
 // Split tiles of an FP32 launch with fewer tiles than CTAs: each CTA takes at least this many
 // k-blocks, so a 128 x 128 tile is summed from a few partial tiles, not from one per k-block.
 constexpr int kMinSplitRunF32 = 4;
@@ -621,23 +620,22 @@ int trmm_entry(gfip_handle_t handle, char side, char uplo, char transa, char dia
 template <typename T>
 size_t trsm_workspace_impl(Handle *h, char side, int64_t m, int64_t n)
 {
-    // every update is at most all of B (m x n) against one panel or one block of unknowns,
-    // and its plan's workspace grows with each dimension
+    // every update is at most all of B (m x n) against one panel of unknowns, and its plan's
+    // workspace grows with each dimension
     const bool left = side == 'L' || side == 'l';
     const int na = (int)(left ? m : n);
     const Plan<T> panel =
-        make_plan<T>(h, Variant::Fused, (int)m, (int)n, std::min(kTrsmPanel, na));
-    const Plan<T> block =
-        make_plan<T>(h, Variant::Fused, (int)m, (int)n, std::min(gfip::TRSM_NB, na));
-    return std::max(total_bytes(h, panel), total_bytes(h, block));
+        make_plan<T>(h, Variant::Fused, (int)m, (int)n, std::min(gfip::TRSM_PANEL, na));
+    return total_bytes(h, panel);
 }
 
-// TRSM, blocked: B := alpha B, then over the diagonal blocks of op(A) in solve order
-// (forward for a lower triangular system, backward for an upper one; for side 'R' the system
-// of each row of X is op(A)^T): solve the block's unknowns for every right-hand side
-// (trsm_diag_kernel), then subtract their contribution from unknowns still to be solved
-// with fused GEMMs (alpha = -1, beta = 1) that pack the solved rows of X (and the panel of
-// op(A)) once for all their tiles.  Only the triangle of A is read.
+// TRSM, blocked: B := alpha B, then over panels of op(A)'s diagonal in solve order (forward
+// for a lower triangular system, backward for an upper one; for side 'R' the system of each
+// row of X is op(A)^T): solve the panel's unknowns for every right-hand side in one launch
+// (trsm::panel_kernel), then subtract their contribution from the unknowns still to be
+// solved with one fused GEMM (alpha = -1, beta = 1, k = the panel's width) that packs the
+// solved rows of X (and the panel of op(A)) once for all its tiles.  Only the triangle of A
+// is read.
 template <typename T>
 int trsm_entry(gfip_handle_t handle, char side, char uplo, char transa, char diag, int64_t m,
                int64_t n, T alpha, const T *A, int64_t lda, T *B, int64_t ldb)
@@ -685,32 +683,18 @@ int trsm_entry(gfip_handle_t handle, char side, char uplo, char transa, char dia
                               T(-1), B + (int64_t)k0 * ldb, ldb, ap, lda, T(1),
                               B + (int64_t)r0 * ldb, ldb);
     };
-    // Two levels: panels of kTrsmPanel unknowns in solve order; inside a panel, blocks of
-    // TRSM_NB solved by substitution, each followed by an update of the panel's unknowns
-    // still to be solved; after the panel, one update of all unknowns outside it still to be
-    // solved (k = kTrsmPanel, long enough runs for the GEMM's pipelines, instead of one short
-    // k = TRSM_NB update of all of them per block).
-    const int npanels = (na + kTrsmPanel - 1) / kTrsmPanel;
+    const int npanels = (na + gfip::TRSM_PANEL - 1) / gfip::TRSM_PANEL;
     for (int ps = 0; ps < npanels; ++ps) {
         const int pi = lower_t ? ps : npanels - 1 - ps;
-        const int p0 = pi * kTrsmPanel;
-        const int pw = std::min(kTrsmPanel, na - p0);
-        const int nblocks = (pw + gfip::TRSM_NB - 1) / gfip::TRSM_NB;
-        for (int step = 0; step < nblocks; ++step) {
-            const int kbi = lower_t ? step : nblocks - 1 - step;
-            const int k0 = p0 + kbi * gfip::TRSM_NB;
-            const int kb = std::min(gfip::TRSM_NB, p0 + pw - k0);
-            // the block's unknowns: rows k0.. of B (side L) or its columns k0.. (side R)
-            cudaError_t e =
-                left ? gfip::launch_trsm_diag<T>(B + k0, ldb, 1, (int)n, A, lda, trans, k0, kb,
-                                                 lower_t, 0, unit, h->stream)
-                     : gfip::launch_trsm_diag<T>(B + (int64_t)k0 * ldb, 1, ldb, (int)m, A, lda,
-                                                 trans, k0, kb, lower_t, 1, unit, h->stream);
-            if (e != cudaSuccess) return GFIP_ERR_CUDA;
-            // the panel's unknowns still to be solved: after the block (forward) or before it
-            const int rc = lower_t ? update(k0, kb, k0 + kb, p0 + pw) : update(k0, kb, p0, k0);
-            if (rc != GFIP_OK) return rc;
-        }
+        const int p0 = pi * gfip::TRSM_PANEL;
+        const int pw = std::min(gfip::TRSM_PANEL, na - p0);
+        // the panel's unknowns: rows p0.. of B (side L) or its columns p0.. (side R)
+        const cudaError_t e =
+            left ? gfip::launch_trsm_panel<T>(B + p0, ldb, 1, (int)n, A, lda, trans, p0, pw,
+                                              lower_t, 0, unit, h->stream)
+                 : gfip::launch_trsm_panel<T>(B + (int64_t)p0 * ldb, 1, ldb, (int)m, A, lda,
+                                              trans, p0, pw, lower_t, 1, unit, h->stream);
+        if (e != cudaSuccess) return GFIP_ERR_CUDA;
         const int rc = lower_t ? update(p0, pw, p0 + pw, na) : update(p0, pw, 0, p0);
         if (rc != GFIP_OK) return rc;
     }

@@ -155,14 +155,14 @@ struct OzakiParams {
 cudaError_t launch_ozaki(const OzakiParams &p, cudaStream_t s);
 size_t ozaki_smem_bytes();
 
-// Triangular solve (gfip_trsm.cu): diagonal blocks of at most TRSM_NB unknowns are solved by
-// substitution, one thread per right-hand side; vector v's element i is B[v*vstride +
-// i*estride].  The system matrix is op(A)'s block at (k0, k0), transposed for side 'R'.
-constexpr int TRSM_NB = 64;
+// Triangular solve (gfip_trsm.cu): one launch solves a panel of at most TRSM_PANEL unknowns
+// (op(A)'s diagonal block at (k0, k0), transposed for side 'R') for every right-hand side;
+// vector v's element i is B[v*vstride + i*estride].
+constexpr int TRSM_PANEL = 512;
 template <typename T>
-cudaError_t launch_trsm_diag(T *B, int64_t vstride, int64_t estride, int nvec, const T *A,
-                             int64_t lda, int a_trans, int k0, int nb, int lower_t,
-                             int transpose_t, int unit, cudaStream_t s);
+cudaError_t launch_trsm_panel(T *B, int64_t vstride, int64_t estride, int nvec, const T *A,
+                              int64_t lda, int a_trans, int k0, int pw, int lower_t,
+                              int transpose_t, int unit, cudaStream_t s);
 
 // Grouped GEMM (gfip_grouped.cu): many independent problems in one persistent launch, each
 // problem with its own warp-tile shape and k-split factor.

@@ -1,115 +1,337 @@
-// gfip_trsm.cu -- the diagonal-block solves of the blocked triangular solve (TRSM).
+// gfip_trsm.cu -- the panel solves of the blocked triangular solve (TRSM).
 //
-// TRSM runs as a sequence over the diagonal blocks of op(A) (see gfip_api.cu): each step
-// solves one block of at most TRSM_NB unknowns for every right-hand side with the kernel
-// below, then the fused GEMM kernel subtracts that block's contribution from the unknowns
-// still to be solved.  The block's triangle is staged in shared memory (only the entries a
-// triangular solve reads: never the other triangle, nor a unit diagonal); one thread runs the
-// substitution for one right-hand side, on a copy of the block's rows of it in shared memory.
+// TRSM runs as a sequence over panels of op(A)'s diagonal (see gfip_api.cu): each step solves
+// one panel of at most TRSM_PANEL unknowns for every right-hand side with the kernel below,
+// then the fused GEMM kernel subtracts the panel's contribution from the unknowns still to be
+// solved.  The kernel solves a panel by column-oriented substitution: once unknown d is known
+// (divided by its diagonal entry), every unknown below it loses its multiple at once.  A warp
+// holds a few right-hand sides, one element of each per lane and 32-row group, in registers;
+// the panel's triangle streams through shared memory in chunks of columns, double-buffered,
+// shared by the CTA's warps, the next chunk's copies issued a part per step of this one.
+// Only the entries a triangular solve reads are read: never the other triangle, nor a unit
+// diagonal.
 #include <cstdint>
 
 #include "gfip_internal.h"
 
 namespace gfip {
+namespace trsm {
 
-// Right-hand sides per CTA (one warp): the block's rows of them are staged in shared memory
-// with coalesced loads (the unit-stride direction of B runs across the threads), solved
-// there, and written back the same way.
-constexpr int TRSM_VPC = 32;
+// Right-hand sides per warp (two: every shared-memory read of the triangle serves both) and
+// warps per CTA (eight, whose substitution chains interleave); 16 right-hand sides per CTA.
+template <typename T> struct Width {
+    static constexpr int RPW = 2;
+    static constexpr int WARPS = 16 / RPW;
+    static constexpr int THREADS = WARPS * 32;
+    static_assert(THREADS == 256 && TRSM_PANEL <= 2 * THREADS, "a part is two loads a thread");
+};
+constexpr int RPC = 16;                   // right-hand sides per CTA
+constexpr int ROWS = TRSM_PANEL / 32;     // 32-row groups of a panel: registers per vector
+constexpr int CW = 16;                    // triangle columns per staged chunk
+constexpr size_t BUF = (size_t)CW * TRSM_PANEL;   // elements of one chunk buffer
+static_assert(TRSM_PANEL % 32 == 0 && 32 % CW == 0, "a 32-row group is whole chunks");
+static_assert(ROWS == 16, "the group update below is written out for 16 groups");
+// two chunk buffers, two diagonals and two reciprocal diagonals
+template <typename T> constexpr size_t smem_bytes() { return sizeof(T) * (2 * BUF + 4 * CW); }
 
-template <typename T> constexpr size_t trsm_diag_smem()
+// The panel's system in solve order: unknown q of the local lower triangular system is row
+// lower_t ? q : pw - 1 - q of the block, so an upper triangular block is solved by the same
+// forward loop.  t(r, c) = op(A)[k0 + r, k0 + c] (side 'L') or op(A)[k0 + c, k0 + r] (side
+// 'R', transpose_t), op(A)[i, j] = A[i + j lda] ('N') or A[j + i lda] ('T').
+struct Panel {
+    const void *A;
+    int64_t lda;
+    int a_trans, transpose_t, lower_t, unit;
+    int k0, pw;
+    __device__ __forceinline__ int row(int q) const { return lower_t ? q : pw - 1 - q; }
+    template <typename T> __device__ __forceinline__ const T *at(int q, int d) const
+    {
+        const int rq = row(q), rd = row(d);
+        const int64_t i = k0 + (transpose_t ? rd : rq), j = k0 + (transpose_t ? rq : rd);
+        const T *a = static_cast<const T *>(A);
+        return a_trans ? a + j + i * lda : a + i + j * lda;
+    }
+};
+
+// Staging of chunk [d0, d0 + CW) of the strictly lower part of the local system:
+// buf[dd * TRSM_PANEL + q] = t(q, d0 + dd) for q > d0 + dd, zero elsewhere (rows from the
+// chunk's 32-row group on), and its diagonal (unless unit).  A chunk is CW parts: where A is
+// contiguous along q a part is one column of the chunk, otherwise a slice of its rows, so
+// that a warp's loads are consecutive in A either way; a part is at most two elements per
+// thread.  Plain loads into registers, issued a chunk ahead and stored to shared memory
+// after the work they hide behind (element copies through cp.async cost more issue slots).
+constexpr int HALF = CW / 2;   // parts loaded together
+template <typename T> struct Stage {
+    T v[HALF][2];
+    T diag;
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_slot(const Panel &p, int d0, int part, int i, int tid,
+                                           int &q, int &dd)
 {
-    return sizeof(T) * (size_t)TRSM_NB * TRSM_NB + sizeof(T) * (size_t)TRSM_NB * (TRSM_VPC + 1);
+    constexpr int THREADS = 256;
+    const int qlo = d0 & ~31, qhi = (p.pw + 31) & ~31;
+    const int e = tid + THREADS * i;
+    if (p.a_trans == p.transpose_t) {
+        dd = part;
+        q = qlo + e;
+        if (q >= qhi) q = -1;
+    } else {
+        const int rows = (qhi - qlo) / CW;
+        dd = e % CW;
+        const int qo = e / CW;
+        q = qo < rows ? qlo + part * rows + qo : -1;
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TRSM_VPC)
-    trsm_diag_kernel(T *B, int64_t vstride, int64_t estride, int nvec, const T *A, int64_t lda,
-                     int a_trans, int k0, int nb, int lower_t, int transpose_t, int unit)
+__device__ __forceinline__ void stage_load(const Panel &p, int d0, int part0, int tid,
+                                           Stage<T> &st)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    // t(r, c) = op(A)[k0 + r, k0 + c] (side 'L') or op(A)[k0 + c, k0 + r] (side 'R'),
-    // op(A)[i, j] = A[i + j lda] ('N') or A[j + i lda] ('T'); read by all threads at once
-    T(*t)[TRSM_NB] = reinterpret_cast<T(*)[TRSM_NB]>(smem);
-    // xs(i, v) = element i of right-hand side v0 + v (padded: conflict-free along i and v)
-    T(*xs)[TRSM_VPC + 1] =
-        reinterpret_cast<T(*)[TRSM_VPC + 1]>(smem + sizeof(T) * TRSM_NB * TRSM_NB);
-    const int tid = threadIdx.x;
-    const int v0 = blockIdx.x * TRSM_VPC;
-    const int nv = min(TRSM_VPC, nvec - v0);
-    for (int e = tid; e < nb * nb; e += TRSM_VPC) {
-        const int r = e / nb, c = e % nb;
-        const bool need = (lower_t ? r > c : r < c) || (r == c && !unit);
-        T v = T(0);
-        if (need) {
-            const int oi = k0 + (transpose_t ? c : r), oj = k0 + (transpose_t ? r : c);
-            v = a_trans ? A[oj + (int64_t)oi * lda] : A[oi + (int64_t)oj * lda];
+#pragma unroll
+    for (int k = 0; k < HALF; ++k)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            int q, dd;
+            stage_slot<T>(p, d0, part0 + k, i, tid, q, dd);
+            const int d = d0 + dd;
+            st.v[k][i] = (q > d && q < p.pw) ? *p.at<T>(q, d) : T(0);
         }
-        t[r][c] = v;
+    if (part0 == 0 && tid < CW) {
+        const int d = d0 + tid;
+        st.diag = (!p.unit && d < p.pw) ? *p.at<T>(d, d) : T(1);
     }
-    // element i of vector v sits at B[v vstride + i estride]; one of the strides is 1
-    const bool along_i = (estride == 1);
-    for (int e = tid; e < nb * nv; e += TRSM_VPC) {
-        const int i = along_i ? e % nb : e / nv, v = along_i ? e / nb : e % nv;
-        xs[i][v] = B[(int64_t)(v0 + v) * vstride + (int64_t)i * estride];
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_store(const Panel &p, int d0, int part0, int tid,
+                                            const Stage<T> &st, T *buf, T *dg)
+{
+#pragma unroll
+    for (int k = 0; k < HALF; ++k)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            int q, dd;
+            stage_slot<T>(p, d0, part0 + k, i, tid, q, dd);
+            if (q >= 0) buf[dd * TRSM_PANEL + q] = st.v[k][i];
+        }
+    if (part0 == 0 && tid < CW) dg[tid] = st.diag;
+}
+
+// b / t from r = RN(1 / t): the product corrected by one exact residual step (an FMA gives
+// b - t q0 exactly), which lands on the correctly rounded quotient or next to it; a zero or
+// non-finite t, or a non-finite result, takes the division itself (its IEEE special values).
+template <typename T> __device__ __noinline__ T divide(T b, T t) { return b / t; }
+
+template <typename T> __device__ __forceinline__ T quotient(T b, T t, T r)
+{
+    const T q0 = b * r;
+    const T q = fma(fma(-t, q0, b), r, q0);
+    // a call, so that the division is never evaluated on the common path
+    if (__builtin_expect(!(isfinite(q) && isfinite(r) && t != T(0)), 0)) return divide(b, t);
+    return q;
+}
+
+// b[R][w] -= tq x[w] for this lane's element of group R of every right-hand side.
+template <typename T, int R, int RPW>
+__device__ __forceinline__ void update_group(T (&b)[ROWS][RPW], T tq, const T (&x)[RPW])
+{
+#pragma unroll
+    for (int w = 0; w < RPW; ++w) b[R][w] = fma(-tq, x[w], b[R][w]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(Width<T>::THREADS, 1)
+    panel_kernel(T *B, int64_t vstride, int64_t estride, int nvec, const Panel p)
+{
+    constexpr int RPW = Width<T>::RPW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *bufs = reinterpret_cast<T *>(smem_raw);
+    T *dgs = bufs + 2 * BUF;     // [2][CW] diagonal entries
+    T *drs = dgs + 2 * CW;       // [2][CW] their reciprocals
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int pw = p.pw;
+
+    // element q of right-hand side w (this warp's) is b[q / 32][w] on lane q % 32; element i
+    // of vector v sits at B[v vstride + i estride]
+    T b[ROWS][RPW];
+    int vec[RPW];
+#pragma unroll
+    for (int w = 0; w < RPW; ++w) vec[w] = blockIdx.x * RPC + warp * RPW + w;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int w = 0; w < RPW; ++w) {
+            const int q = 32 * r + lane;
+            b[r][w] = (q < pw && vec[w] < nvec)
+                          ? B[(int64_t)vec[w] * vstride + (int64_t)p.row(q) * estride]
+                          : T(0);
+        }
+
+    {
+        Stage<T> st;
+        stage_load<T>(p, 0, 0, tid, st);
+        stage_store<T>(p, 0, 0, tid, st, bufs, dgs);
+        stage_load<T>(p, 0, HALF, tid, st);
+        stage_store<T>(p, 0, HALF, tid, st, bufs, dgs);
     }
-    __syncthreads();
-    if (tid < nv) {
-        for (int q = 0; q < nb; ++q) {
-            const int i = lower_t ? q : nb - 1 - q;
-            T s = xs[i][tid];
-            for (int d = 0; d < q; ++d) {
-                const int c = lower_t ? d : nb - 1 - d;
-                s -= t[i][c] * xs[c][tid];
+    // The groups run in a loop, not unrolled (the code stays small enough for the instruction
+    // cache): the group being solved moves into cur[] and back; the later groups are
+    // updated in an unrolled loop over all groups, skipping the ones not after it.
+    int ch = 0;   // chunks begun
+#pragma unroll 1
+    for (int r = 0; r < ROWS; ++r) {
+        if (32 * r >= pw) break;
+        T cur[RPW];
+#pragma unroll
+        for (int rr = 0; rr < ROWS; ++rr)
+            if (rr == r) {
+#pragma unroll
+                for (int w = 0; w < RPW; ++w) cur[w] = b[rr][w];
             }
-            if (!unit) s = s / t[i][i];
-            xs[i][tid] = s;
+#pragma unroll 1
+        for (int h = 0; h < 32 / CW; ++h) {
+            const int d0 = 32 * r + h * CW;
+            if (d0 >= pw) break;
+            __syncthreads();      // chunk ch is in shared memory
+            const T *tb = bufs + (ch & 1) * BUF;
+            const T *dg = dgs + (ch & 1) * CW;
+            T *dr = drs + (ch & 1) * CW;
+            if (tid < CW) dr[tid] = p.unit ? T(1) : T(1) / dg[tid];
+            __syncthreads();
+            const bool more = d0 + CW < pw;   // a next chunk to stage meanwhile
+            T *nbuf = bufs + ((ch + 1) & 1) * BUF;
+            T *ndg = dgs + ((ch + 1) & 1) * CW;
+            Stage<T> st;
+            if (more) stage_load<T>(p, d0 + CW, 0, tid, st);
+            const int dn = min(CW, pw - d0);
+            // the chunk's unknowns one after another; each updates only the later unknowns
+            // of its own 32-row group here (the chain's latency is the solve's floor)
+            for (int dd = 0; dd < dn; ++dd) {
+                const int owner = h * CW + dd;   // the lane holding unknown d0 + dd
+                const T t = dg[dd], rt = dr[dd];
+                const T tq = tb[dd * TRSM_PANEL + 32 * r + lane];
+#pragma unroll
+                for (int w = 0; w < RPW; ++w) {
+                    T bc = cur[w];
+                    if (!p.unit && lane == owner) bc = quotient(bc, t, rt);
+                    const T x = __shfl_sync(0xffffffffu, bc, owner);
+                    if (lane == owner) cur[w] = x;
+                    if (lane > owner) cur[w] = fma(-tq, x, cur[w]);
+                }
+            }
+            if (more) {
+                stage_store<T>(p, d0 + CW, 0, tid, st, nbuf, ndg);
+                stage_load<T>(p, d0 + CW, HALF, tid, st);
+            }
+            // then the chunk's unknowns leave the later groups, in the same order (the
+            // multiply-adds of every element still run in increasing column order), free of
+            // the chain: every group and right-hand side an independent accumulation
+            for (int dd = 0; dd < dn; ++dd) {
+                const int owner = h * CW + dd;
+                T x[RPW];
+#pragma unroll
+                for (int w = 0; w < RPW; ++w) x[w] = __shfl_sync(0xffffffffu, cur[w], owner);
+                const T *col = tb + dd * TRSM_PANEL + lane;
+                if constexpr (sizeof(T) == 4) {
+                    // every group in one unrolled pass, the ones not after r predicated off
+                    // (cheap on the FMA pipe, and the loads schedule ahead of their use)
+#pragma unroll
+                    for (int rr = 1; rr < ROWS; ++rr)
+                        if (rr > r && 32 * rr < pw) {
+                            const T tq = col[32 * rr];
+#pragma unroll
+                            for (int w = 0; w < RPW; ++w) b[rr][w] = fma(-tq, x[w], b[rr][w]);
+                        }
+                    continue;
+                }
+                // FP64: a predicated-off multiply-add still takes the scarce DFMA pipe, so
+                // enter at the first later group and fall through the rest
+                switch (r) {
+#define GFIP_TRSM_GROUP(R)                                                                  \
+    case R - 1:                                                                             \
+        if (32 * R < pw) update_group<T, R, RPW>(b, col[32 * R], x);                       \
+        [[fallthrough]];
+                    GFIP_TRSM_GROUP(1) GFIP_TRSM_GROUP(2) GFIP_TRSM_GROUP(3)
+                    GFIP_TRSM_GROUP(4) GFIP_TRSM_GROUP(5) GFIP_TRSM_GROUP(6)
+                    GFIP_TRSM_GROUP(7) GFIP_TRSM_GROUP(8) GFIP_TRSM_GROUP(9)
+                    GFIP_TRSM_GROUP(10) GFIP_TRSM_GROUP(11) GFIP_TRSM_GROUP(12)
+                    GFIP_TRSM_GROUP(13) GFIP_TRSM_GROUP(14) GFIP_TRSM_GROUP(15)
+#undef GFIP_TRSM_GROUP
+                default: break;
+                }
+            }
+            if (more) stage_store<T>(p, d0 + CW, HALF, tid, st, nbuf, ndg);
+            __syncthreads();   // this buffer is restaged during the next chunk
+            ++ch;
         }
+#pragma unroll
+        for (int rr = 0; rr < ROWS; ++rr)
+            if (rr == r) {
+#pragma unroll
+                for (int w = 0; w < RPW; ++w) b[rr][w] = cur[w];
+            }
     }
-    __syncthreads();
-    for (int e = tid; e < nb * nv; e += TRSM_VPC) {
-        const int i = along_i ? e % nb : e / nv, v = along_i ? e / nb : e % nv;
-        B[(int64_t)(v0 + v) * vstride + (int64_t)i * estride] = xs[i][v];
-    }
+
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int w = 0; w < RPW; ++w) {
+            const int q = 32 * r + lane;
+            if (q < pw && vec[w] < nvec)
+                B[(int64_t)vec[w] * vstride + (int64_t)p.row(q) * estride] = b[r][w];
+        }
 }
 
+}  // namespace trsm
+
 template <typename T>
-cudaError_t launch_trsm_diag_impl(T *B, int64_t vstride, int64_t estride, int nvec, const T *A,
-                                  int64_t lda, int a_trans, int k0, int nb, int lower_t,
-                                  int transpose_t, int unit, cudaStream_t s)
+cudaError_t launch_trsm_panel_impl(T *B, int64_t vstride, int64_t estride, int nvec,
+                                   const T *A, int64_t lda, int a_trans, int k0, int pw,
+                                   int lower_t, int transpose_t, int unit, cudaStream_t s)
 {
-    if (nvec <= 0 || nb <= 0) return cudaSuccess;
-    if (nb > TRSM_NB) return cudaErrorInvalidValue;
+    if (nvec <= 0 || pw <= 0) return cudaSuccess;
+    if (pw > TRSM_PANEL) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
-        const cudaError_t e = cudaFuncSetAttribute(trsm_diag_kernel<T>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   static_cast<int>(trsm_diag_smem<T>()));
+        const cudaError_t e = cudaFuncSetAttribute(
+            trsm::panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            static_cast<int>(trsm::smem_bytes<T>()));
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int blocks = (nvec + TRSM_VPC - 1) / TRSM_VPC;
-    trsm_diag_kernel<T><<<blocks, TRSM_VPC, trsm_diag_smem<T>(), s>>>(
-        B, vstride, estride, nvec, A, lda, a_trans, k0, nb, lower_t, transpose_t, unit);
+    trsm::Panel p;
+    p.A = A;
+    p.lda = lda;
+    p.a_trans = a_trans;
+    p.transpose_t = transpose_t;
+    p.lower_t = lower_t;
+    p.unit = unit;
+    p.k0 = k0;
+    p.pw = pw;
+    const int blocks = (nvec + trsm::RPC - 1) / trsm::RPC;
+    trsm::panel_kernel<T><<<blocks, trsm::Width<T>::THREADS, trsm::smem_bytes<T>(), s>>>(
+        B, vstride, estride, nvec, p);
     return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_trsm_diag<double>(double *B, int64_t vstride, int64_t estride, int nvec,
-                                     const double *A, int64_t lda, int a_trans, int k0, int nb,
-                                     int lower_t, int transpose_t, int unit, cudaStream_t s)
+cudaError_t launch_trsm_panel<double>(double *B, int64_t vstride, int64_t estride, int nvec,
+                                      const double *A, int64_t lda, int a_trans, int k0, int pw,
+                                      int lower_t, int transpose_t, int unit, cudaStream_t s)
 {
-    return launch_trsm_diag_impl<double>(B, vstride, estride, nvec, A, lda, a_trans, k0, nb,
-                                         lower_t, transpose_t, unit, s);
+    return launch_trsm_panel_impl<double>(B, vstride, estride, nvec, A, lda, a_trans, k0, pw,
+                                          lower_t, transpose_t, unit, s);
 }
 
 template <>
-cudaError_t launch_trsm_diag<float>(float *B, int64_t vstride, int64_t estride, int nvec,
-                                    const float *A, int64_t lda, int a_trans, int k0, int nb,
-                                    int lower_t, int transpose_t, int unit, cudaStream_t s)
+cudaError_t launch_trsm_panel<float>(float *B, int64_t vstride, int64_t estride, int nvec,
+                                     const float *A, int64_t lda, int a_trans, int k0, int pw,
+                                     int lower_t, int transpose_t, int unit, cudaStream_t s)
 {
-    return launch_trsm_diag_impl<float>(B, vstride, estride, nvec, A, lda, a_trans, k0, nb,
-                                        lower_t, transpose_t, unit, s);
+    return launch_trsm_panel_impl<float>(B, vstride, estride, nvec, A, lda, a_trans, k0, pw,
+                                         lower_t, transpose_t, unit, s);
 }
 
 }  // namespace gfip
