@@ -24,6 +24,7 @@ constexpr size_t kHeader = 256;             // status word, launch counters, spa
 constexpr size_t kLaunchCountOffset = 64;   // header word: GEMM launches so far (epochs)
 constexpr size_t kDoneCountOffset = 128;    // header word: finished CTAs of the running launch
 constexpr size_t kPackCountOffset = 192;    // header word: tiles packed by shared packing
+constexpr size_t kTileNextOffset = 32;      // header word: data-parallel tiles taken
 constexpr size_t kCtrlGranule = 64 * 1024;  // control region grows in these steps
 constexpr int kMinSplitRun = 8;              // shortest k run per CTA in a split wave
 // Split tiles of an FP32 launch with fewer tiles than CTAs: each CTA takes at least this many
@@ -355,6 +356,7 @@ int launch_plan(Handle *h, Variant v, int tri, char transa, char transb, int64_t
     p.launch_count = reinterpret_cast<unsigned int *>(h->ws + kLaunchCountOffset);
     p.done_count = reinterpret_cast<unsigned int *>(h->ws + kDoneCountOffset);
     p.pack_count = reinterpret_cast<unsigned long long *>(h->ws + kPackCountOffset);
+    p.tile_next = reinterpret_cast<unsigned long long *>(h->ws + kTileNextOffset);
 
     int launches = 0;
     if (v == Variant::PackThenCompute) {

@@ -103,7 +103,7 @@ template <typename T> struct GemmParams {
     int tmask_a;      // triangular mask of op(A) (TRMM), 0 = dense; see TriMask
     int tmask_b;      // triangular mask of op(B)
     int grid;         // persistent CTAs
-    int dp_tiles;     // tiles [0, dp_tiles) are data-parallel: tile t runs on CTA t % grid
+    int dp_tiles;     // tiles [0, dp_tiles) are data-parallel, taken in order from tile_next
     int64_t sk_iters; // (tiles - dp_tiles) * kt iterations split evenly over the CTAs
     int mode_a, mode_b;
     unsigned long long *state_a;     // [mt * kt] epoch-tagged ready words of packed A tiles,
@@ -117,6 +117,7 @@ template <typename T> struct GemmParams {
     unsigned int *launch_count;      // launches so far (the epoch of a launch is this + 1)
     unsigned int *done_count;        // CTAs of the current launch that have finished
     unsigned long long *pack_count;  // shared packing: epoch-tagged count of packed tiles
+    unsigned long long *tile_next;   // epoch-tagged count of data-parallel tiles taken
 };
 
 // Parameters of the pack kernel of the pack-then-compute variant.

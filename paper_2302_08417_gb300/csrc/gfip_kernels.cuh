@@ -414,6 +414,7 @@ template <typename T, typename C = TileCfg<T>> struct GemmSmem {
     int mode_a, mode_b;  // the segment's operand modes after the reuse logic (reused_a/_b)
     int watch;           // shared packing: the count of packed tiles is not complete yet
     int flag;
+    int next_tile;       // the data-parallel tile this CTA takes next
 };
 
 // Loads one 16-byte chunk (CH elements) from shared memory.
@@ -1026,11 +1027,26 @@ struct Kernel {
         const int g = blockIdx.x;
         T acc[TM][TN];
         if (!TMASK && p.shared_pack) share_pack(p, sm, epoch);
-        for (int t = g; t < p.dp_tiles; t += p.grid) {
+        // Data-parallel tiles in order: CTA g takes tile g first, then tiles grid, grid + 1,
+        // ... from a launch-wide counter (epoch-tagged, so nothing is cleared between
+        // launches), so a CTA slowed by extra work, such as a producer's pack stores, takes
+        // fewer tiles and the CTAs reach the split wave together.  Thread 0 asks for its next
+        // tile while the current one runs.  Tile t still starts in round about t / grid, the
+        // round the reuse logic (reused_a/_b) reckons with.
+        const unsigned long long tag = static_cast<unsigned long long>(epoch) << 32;
+        bool first = true;
+        for (int t = g; t < p.dp_tiles; t = sm.next_tile) {
+            unsigned long long next = 0;
+            if (threadIdx.x == 0) {
+                if (first) atomicMax(p.tile_next, tag);   // ordered before the add below
+                next = atomicAdd(p.tile_next, 1ull);
+            }
+            first = false;
             int i, j;
             tile_of(p, t, i, j);
-            run_segment(p, sm, i, j, 0, p.kt, acc, epoch);
+            run_segment(p, sm, i, j, 0, p.kt, acc, epoch);   // its barriers order t's reads
             epilogue(p, i, j, acc);
+            if (threadIdx.x == 0) sm.next_tile = p.grid + static_cast<int>(next - tag);
             __syncthreads();
         }
         if (p.sk_iters > 0) {
