@@ -5,7 +5,7 @@
 // then the fused GEMM kernel subtracts the panel's contribution from the unknowns still to be
 // solved.  The kernel solves a panel by column-oriented substitution: once unknown d is known
 // (divided by its diagonal entry), every unknown below it loses its multiple at once.  A warp
-// holds a few right-hand sides, one element of each per lane and 32-row group, in registers;
+// holds one right-hand side, one element per lane and 32-row group, in registers;
 // the panel's triangle streams through shared memory in chunks of columns, double-buffered,
 // shared by the CTA's warps, the next chunk's copies issued a part per step of this one.
 // Only the entries a triangular solve reads are read: never the other triangle, nor a unit
@@ -17,13 +17,17 @@
 namespace gfip {
 namespace trsm {
 
-// Right-hand sides per warp (two: every shared-memory read of the triangle serves both) and
-// warps per CTA (eight, whose substitution chains interleave); 16 right-hand sides per CTA.
+// Right-hand sides per warp (one: a warp's substitution chain is as short as it gets, and
+// sixteen warps per CTA interleave their chains; two measured 2.5 % slower at 2048 x 2048);
+// 16 right-hand sides per CTA.  (Overridable at build time for such measurements.)
+#ifndef GFIP_TRSM_RPW
+#define GFIP_TRSM_RPW 1
+#endif
 template <typename T> struct Width {
-    static constexpr int RPW = 2;
+    static constexpr int RPW = GFIP_TRSM_RPW;
     static constexpr int WARPS = 16 / RPW;
     static constexpr int THREADS = WARPS * 32;
-    static_assert(THREADS == 256 && TRSM_PANEL <= 2 * THREADS, "a part is two loads a thread");
+    static constexpr int SLOTS = (TRSM_PANEL + THREADS - 1) / THREADS;   // loads a part takes
 };
 constexpr int RPC = 16;                   // right-hand sides per CTA
 constexpr int ROWS = TRSM_PANEL / 32;     // 32-row groups of a panel: registers per vector
@@ -57,12 +61,12 @@ struct Panel {
 // buf[dd * TRSM_PANEL + q] = t(q, d0 + dd) for q > d0 + dd, zero elsewhere (rows from the
 // chunk's 32-row group on), and its diagonal (unless unit).  A chunk is CW parts: where A is
 // contiguous along q a part is one column of the chunk, otherwise a slice of its rows, so
-// that a warp's loads are consecutive in A either way; a part is at most two elements per
+// that a warp's loads are consecutive in A either way; a part is at most SLOTS elements per
 // thread.  Plain loads into registers, issued a chunk ahead and stored to shared memory
 // after the work they hide behind (element copies through cp.async cost more issue slots).
 constexpr int HALF = CW / 2;   // parts loaded together
 template <typename T> struct Stage {
-    T v[HALF][2];
+    T v[HALF][Width<T>::SLOTS];
     T diag;
 };
 
@@ -70,9 +74,8 @@ template <typename T>
 __device__ __forceinline__ void stage_slot(const Panel &p, int d0, int part, int i, int tid,
                                            int &q, int &dd)
 {
-    constexpr int THREADS = 256;
     const int qlo = d0 & ~31, qhi = (p.pw + 31) & ~31;
-    const int e = tid + THREADS * i;
+    const int e = tid + Width<T>::THREADS * i;
     if (p.a_trans == p.transpose_t) {
         dd = part;
         q = qlo + e;
@@ -92,7 +95,7 @@ __device__ __forceinline__ void stage_load(const Panel &p, int d0, int part0, in
 #pragma unroll
     for (int k = 0; k < HALF; ++k)
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < Width<T>::SLOTS; ++i) {
             int q, dd;
             stage_slot<T>(p, d0, part0 + k, i, tid, q, dd);
             const int d = d0 + dd;
@@ -111,7 +114,7 @@ __device__ __forceinline__ void stage_store(const Panel &p, int d0, int part0, i
 #pragma unroll
     for (int k = 0; k < HALF; ++k)
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < Width<T>::SLOTS; ++i) {
             int q, dd;
             stage_slot<T>(p, d0, part0 + k, i, tid, q, dd);
             if (q >= 0) buf[dd * TRSM_PANEL + q] = st.v[k][i];
