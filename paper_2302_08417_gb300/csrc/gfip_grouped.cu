@@ -4,8 +4,8 @@
 // problem size) read for a batch on a GPU: every problem C_g := alpha_g op(A_g) op(B_g) +
 // beta_g C_g, with its own sizes, operand orders and leading dimensions, runs inside ONE
 // persistent launch.  The unit of work is a warp: each warp computes one small tile of one
-// problem at a time, with a double-buffered k-chunk pipeline of its own (element copies of the
-// raw strided operands into a private slice of shared memory, zero-filled at fringes, Sec. 2.2)
+// problem at a time, with a 3-stage k-chunk pipeline of its own (element copies of the raw
+// strided operands into a private slice of shared memory, zero-filled at fringes, Sec. 2.2)
 // and no barrier with any other warp, so an SM keeps many small tiles in flight.  Because the
 // unit is a warp, one launch mixes tile shapes: each problem carries the shape and k-split
 // factor that the autotuner (grouped.py) chose for its size bucket.  A split tile's k-ranges
@@ -19,8 +19,10 @@
 //   scan     one CTA: prefix sums of units, split tiles and partial-sum elements in the
 //            processing order (problems whose partial sums would overflow the workspace run
 //            unsplit), and clears the arrival counters
-//   grouped  persistent warps stride over the global unit list, largest problems first when
-//            the caller orders them so
+//   grouped  persistent warps are dealt the units in bands of all warps, alternately forwards
+//            and backwards, costliest first when the caller orders the problems so; the C tile
+//            of a unit goes through the warp's shared memory, so C is read and written
+//            column by column with lanes along its rows
 #include <climits>
 #include <cstdint>
 #include <type_traits>
