@@ -262,7 +262,9 @@ int gfip_strsm(gfip_handle_t handle, char side, char uplo, char transa, char dia
  * array): its warp tile, and the number of k-ranges (1..8) each of its tiles is split into,
  * computed by different warps and added in k-range order by the last to finish (the result
  * bits depend on the plan, never on timing).  `order` (a device array, or NULL for 0..count-1)
- * is the processing order of the problems, e.g. largest first.  split_elems is the number of
+ * is the processing order of the problems; warps are dealt the work units in bands of all
+ * warps, alternately forwards and backwards, so an order with the costliest units first
+ * (the Python Plan's: units' k-chunks weighted by tile area) ends the warps together.  split_elems is the number of
  * partial-sum elements the plan needs (the sum over split problems of tiles x splits x tile
  * area); the workspace must hold gfip_grouped_plan_workspace_size(count, split_elems) bytes,
  * and a problem whose partial sums would not fit runs unsplit.  The plan is chosen per size
