@@ -4,12 +4,13 @@
 // one panel of at most TRSM_PANEL unknowns for every right-hand side with the kernel below,
 // then the fused GEMM kernel subtracts the panel's contribution from the unknowns still to be
 // solved.  The kernel solves a panel by column-oriented substitution: once unknown d is known
-// (divided by its diagonal entry), every unknown below it loses its multiple at once.  A warp
-// holds one right-hand side, one element per lane and 32-row group, in registers;
-// the panel's triangle streams through shared memory in chunks of columns, double-buffered,
-// shared by the CTA's warps, the next chunk's copies issued a part per step of this one.
-// Only the entries a triangular solve reads are read: never the other triangle, nor a unit
-// diagonal.
+// (divided by its diagonal entry), every unknown below it loses its multiple at once; per
+// chunk of columns the chain updates only its own 32-row group, and the later groups are
+// updated afterwards, off the chain.  A warp holds one right-hand side, one element per lane
+// and 32-row group, in registers; the panel's triangle streams through shared memory in
+// chunks of columns, double-buffered and shared by the CTA's warps, the next chunk loaded
+// into registers while this one is solved.  Only the entries a triangular solve reads are
+// read: never the other triangle, nor a unit diagonal.
 #include <cstdint>
 
 #include "gfip_internal.h"
