@@ -976,6 +976,8 @@ def main():
                     help="only run the grouped-GEMM report on COUNT problems")
     ap.add_argument("--autograd-only", action="store_true",
                     help="only run the differentiable-GEMM report")
+    ap.add_argument("--trsm-only", type=int, default=0, metavar="N",
+                    help="only the TRSM report, on an N x N system with N right-hand sides")
     ap.add_argument("--syrk-only", action="store_true",
                     help="only run the SYRK, TRMM and TRSM reports")
     ap.add_argument("--no-syrk", action="store_true",
@@ -1003,8 +1005,11 @@ def main():
     h = g.Handle()
     h.bind_stream()
     stream = torch.cuda.current_stream()
-    if args.emulation_only or args.batched_only or args.autograd_only or args.syrk_only:
+    if (args.emulation_only or args.batched_only or args.autograd_only or args.syrk_only
+            or args.trsm_only):
         out = {}
+        if args.trsm_only:
+            out["trsm"] = trsm_report(g, torch, shapes=((args.trsm_only, args.trsm_only),))
         if args.syrk_only:
             out["syrk"] = syrk_report(g, torch)
             out["trmm"] = trmm_report(g, torch)
