@@ -137,12 +137,19 @@ template <typename T> __device__ __forceinline__ T quotient(T b, T t, T r)
     return q;
 }
 
-// b[R][w] -= tq x[w] for this lane's element of group R of every right-hand side.
+// b[R][w] -= sum over the chunk's columns dd, in order, of t(32 R + lane, d0 + dd) x[dd][w]:
+// this lane's element of group R of every right-hand side (col = the chunk's staged column 0
+// at the group's first row).
 template <typename T, int R, int RPW>
-__device__ __forceinline__ void update_group(T (&b)[ROWS][RPW], T tq, const T (&x)[RPW])
+__device__ __forceinline__ void update_group(T (&b)[ROWS][RPW], const T *col,
+                                             const T (&x)[CW][RPW])
 {
 #pragma unroll
-    for (int w = 0; w < RPW; ++w) b[R][w] = fma(-tq, x[w], b[R][w]);
+    for (int dd = 0; dd < CW; ++dd) {
+        const T tq = col[dd * TRSM_PANEL];
+#pragma unroll
+        for (int w = 0; w < RPW; ++w) b[R][w] = fma(-tq, x[dd][w], b[R][w]);
+    }
 }
 
 template <typename T>
@@ -231,40 +238,33 @@ __global__ void __launch_bounds__(Width<T>::THREADS, 1)
             }
             // then the chunk's unknowns leave the later groups, in the same order (the
             // multiply-adds of every element still run in increasing column order), free of
-            // the chain: every group and right-hand side an independent accumulation
-            for (int dd = 0; dd < dn; ++dd) {
-                const int owner = h * CW + dd;
-                T x[RPW];
+            // the chain: every group and right-hand side an independent accumulation.  The
+            // chunk's solved unknowns are gathered once; a group's update is then straight-line
+            // code over the chunk's columns, entered at the first later group and falling
+            // through the rest (no instruction for a group that is done).  Columns past the
+            // panel (a short last chunk) hold zeros in the staged triangle and take zero
+            // unknowns here, so they change nothing.
+            T xs[CW][RPW];
 #pragma unroll
-                for (int w = 0; w < RPW; ++w) x[w] = __shfl_sync(0xffffffffu, cur[w], owner);
-                const T *col = tb + dd * TRSM_PANEL + lane;
-                if constexpr (sizeof(T) == 4) {
-                    // every group in one unrolled pass, the ones not after r predicated off
-                    // (cheap on the FMA pipe, and the loads schedule ahead of their use)
+            for (int dd = 0; dd < CW; ++dd)
 #pragma unroll
-                    for (int rr = 1; rr < ROWS; ++rr)
-                        if (rr > r && 32 * rr < pw) {
-                            const T tq = col[32 * rr];
-#pragma unroll
-                            for (int w = 0; w < RPW; ++w) b[rr][w] = fma(-tq, x[w], b[rr][w]);
-                        }
-                    continue;
+                for (int w = 0; w < RPW; ++w) {
+                    const T x = __shfl_sync(0xffffffffu, cur[w], h * CW + dd);
+                    xs[dd][w] = dd < dn ? x : T(0);
                 }
-                // FP64: a predicated-off multiply-add still takes the scarce DFMA pipe, so
-                // enter at the first later group and fall through the rest
-                switch (r) {
+            const T *col = tb + lane;
+            switch (r) {
 #define GFIP_TRSM_GROUP(R)                                                                  \
     case R - 1:                                                                             \
-        if (32 * R < pw) update_group<T, R, RPW>(b, col[32 * R], x);                       \
+        if (32 * R < pw) update_group<T, R, RPW>(b, col + 32 * R, xs);                     \
         [[fallthrough]];
-                    GFIP_TRSM_GROUP(1) GFIP_TRSM_GROUP(2) GFIP_TRSM_GROUP(3)
-                    GFIP_TRSM_GROUP(4) GFIP_TRSM_GROUP(5) GFIP_TRSM_GROUP(6)
-                    GFIP_TRSM_GROUP(7) GFIP_TRSM_GROUP(8) GFIP_TRSM_GROUP(9)
-                    GFIP_TRSM_GROUP(10) GFIP_TRSM_GROUP(11) GFIP_TRSM_GROUP(12)
-                    GFIP_TRSM_GROUP(13) GFIP_TRSM_GROUP(14) GFIP_TRSM_GROUP(15)
+                GFIP_TRSM_GROUP(1) GFIP_TRSM_GROUP(2) GFIP_TRSM_GROUP(3)
+                GFIP_TRSM_GROUP(4) GFIP_TRSM_GROUP(5) GFIP_TRSM_GROUP(6)
+                GFIP_TRSM_GROUP(7) GFIP_TRSM_GROUP(8) GFIP_TRSM_GROUP(9)
+                GFIP_TRSM_GROUP(10) GFIP_TRSM_GROUP(11) GFIP_TRSM_GROUP(12)
+                GFIP_TRSM_GROUP(13) GFIP_TRSM_GROUP(14) GFIP_TRSM_GROUP(15)
 #undef GFIP_TRSM_GROUP
-                default: break;
-                }
+            default: break;
             }
             if (more) stage_store<T>(p, d0 + CW, HALF, tid, st, nbuf, ndg);
             __syncthreads();   // this buffer is restaged during the next chunk
