@@ -18,19 +18,16 @@
 namespace gfip {
 namespace trsm {
 
-// Right-hand sides per warp (one: a warp's substitution chain is as short as it gets, and
-// sixteen warps per CTA interleave their chains; two measured 2.5 % slower at 2048 x 2048);
-// 16 right-hand sides per CTA.  (Overridable at build time for such measurements.)
-#ifndef GFIP_TRSM_RPW
-#define GFIP_TRSM_RPW 1
-#endif
-template <typename T> struct Width {
-    static constexpr int RPW = GFIP_TRSM_RPW;
-    static constexpr int WARPS = 16 / RPW;
-    static constexpr int THREADS = WARPS * 32;
-    static constexpr int SLOTS = (TRSM_PANEL + THREADS - 1) / THREADS;   // loads a part takes
-};
-constexpr int RPC = 16;                   // right-hand sides per CTA
+// One right-hand side per warp: a warp's substitution chain is as short as it gets, and the
+// CTA's warps interleave their chains (two per warp measured 2.5 % slower at 2048 x 2048).
+// FP32 CTAs run 16 warps.  FP64, bound by its DFMA pipe, runs between 8 and 16, as many as
+// spread the right-hand sides over all SMs (2048 of them on 152 SMs: 14 a CTA, 147 CTAs,
+// 11 % faster than 16 a CTA on 128 SMs; the same shape made FP32 5 % slower).
+constexpr int RPW = 1;
+constexpr int MIN_WARPS = 8, MAX_WARPS = 16;
+// loads a staging part takes a thread: one with 16 warps, two with fewer (the kernel is
+// compiled for both)
+constexpr int MAX_SLOTS = TRSM_PANEL / (MIN_WARPS * 32);
 constexpr int ROWS = TRSM_PANEL / 32;     // 32-row groups of a panel: registers per vector
 constexpr int CW = 16;                    // triangle columns per staged chunk
 constexpr size_t BUF = (size_t)CW * TRSM_PANEL;   // elements of one chunk buffer
@@ -42,20 +39,22 @@ template <typename T> constexpr size_t smem_bytes() { return sizeof(T) * (2 * BU
 // The panel's system in solve order: unknown q of the local lower triangular system is row
 // lower_t ? q : pw - 1 - q of the block, so an upper triangular block is solved by the same
 // forward loop.  t(r, c) = op(A)[k0 + r, k0 + c] (side 'L') or op(A)[k0 + c, k0 + r] (side
-// 'R', transpose_t), op(A)[i, j] = A[i + j lda] ('N') or A[j + i lda] ('T').
+// 'R', transpose_t), op(A)[i, j] = A[i + j lda] ('N') or A[j + i lda] ('T').  Every case is
+// linear in (q, d): t(q, d) sits at A[o0 + sgn (q cq + d cd)], the four numbers set on the
+// host (launch_trsm_panel).
 struct Panel {
     const void *A;
-    int64_t lda;
-    int a_trans, transpose_t, lower_t, unit;
+    int64_t o0, cq, cd;
+    int sgn;            // +1 lower, -1 upper (rows counted from the block's end)
+    int lower_t, unit;
     int k0, pw;
     __device__ __forceinline__ int row(int q) const { return lower_t ? q : pw - 1 - q; }
     template <typename T> __device__ __forceinline__ const T *at(int q, int d) const
     {
-        const int rq = row(q), rd = row(d);
-        const int64_t i = k0 + (transpose_t ? rd : rq), j = k0 + (transpose_t ? rq : rd);
-        const T *a = static_cast<const T *>(A);
-        return a_trans ? a + j + i * lda : a + i + j * lda;
+        return static_cast<const T *>(A) + o0 + sgn * ((int64_t)q * cq + (int64_t)d * cd);
     }
+    // along q the copies run along memory (|cq| == 1)
+    __device__ __forceinline__ bool along_q() const { return cq == 1; }
 };
 
 // Staging of chunk [d0, d0 + CW) of the strictly lower part of the local system:
@@ -66,8 +65,8 @@ struct Panel {
 // thread.  Plain loads into registers, issued a chunk ahead and stored to shared memory
 // after the work they hide behind (element copies through cp.async cost more issue slots).
 constexpr int HALF = CW / 2;   // parts loaded together
-template <typename T> struct Stage {
-    T v[HALF][Width<T>::SLOTS];
+template <typename T, int SLOTS> struct Stage {
+    T v[HALF][SLOTS];
     T diag;
 };
 
@@ -76,8 +75,8 @@ __device__ __forceinline__ void stage_slot(const Panel &p, int d0, int part, int
                                            int &q, int &dd)
 {
     const int qlo = d0 & ~31, qhi = (p.pw + 31) & ~31;
-    const int e = tid + Width<T>::THREADS * i;
-    if (p.a_trans == p.transpose_t) {
+    const int e = tid + blockDim.x * i;
+    if (p.along_q()) {
         dd = part;
         q = qlo + e;
         if (q >= qhi) q = -1;
@@ -89,14 +88,14 @@ __device__ __forceinline__ void stage_slot(const Panel &p, int d0, int part, int
     }
 }
 
-template <typename T>
+template <typename T, int SLOTS>
 __device__ __forceinline__ void stage_load(const Panel &p, int d0, int part0, int tid,
-                                           Stage<T> &st)
+                                           Stage<T, SLOTS> &st)
 {
 #pragma unroll
     for (int k = 0; k < HALF; ++k)
 #pragma unroll
-        for (int i = 0; i < Width<T>::SLOTS; ++i) {
+        for (int i = 0; i < SLOTS; ++i) {
             int q, dd;
             stage_slot<T>(p, d0, part0 + k, i, tid, q, dd);
             const int d = d0 + dd;
@@ -108,14 +107,14 @@ __device__ __forceinline__ void stage_load(const Panel &p, int d0, int part0, in
     }
 }
 
-template <typename T>
+template <typename T, int SLOTS>
 __device__ __forceinline__ void stage_store(const Panel &p, int d0, int part0, int tid,
-                                            const Stage<T> &st, T *buf, T *dg)
+                                            const Stage<T, SLOTS> &st, T *buf, T *dg)
 {
 #pragma unroll
     for (int k = 0; k < HALF; ++k)
 #pragma unroll
-        for (int i = 0; i < Width<T>::SLOTS; ++i) {
+        for (int i = 0; i < SLOTS; ++i) {
             int q, dd;
             stage_slot<T>(p, d0, part0 + k, i, tid, q, dd);
             if (q >= 0) buf[dd * TRSM_PANEL + q] = st.v[k][i];
@@ -124,16 +123,18 @@ __device__ __forceinline__ void stage_store(const Panel &p, int d0, int part0, i
 }
 
 // b / t from r = RN(1 / t): the product corrected by one exact residual step (an FMA gives
-// b - t q0 exactly), which lands on the correctly rounded quotient or next to it; a zero or
-// non-finite t, or a non-finite result, takes the division itself (its IEEE special values).
+// b - t q0 exactly), which lands on the correctly rounded quotient or next to it; a
+// non-finite result takes the division itself (its IEEE special values).
 template <typename T> __device__ __noinline__ T divide(T b, T t) { return b / t; }
 
 template <typename T> __device__ __forceinline__ T quotient(T b, T t, T r)
 {
     const T q0 = b * r;
     const T q = fma(fma(-t, q0, b), r, q0);
-    // a call, so that the division is never evaluated on the common path
-    if (__builtin_expect(!(isfinite(q) && isfinite(r) && t != T(0)), 0)) return divide(b, t);
+    // a zero, infinite or NaN t (r infinite, zero or NaN) or a non-finite b makes q
+    // non-finite; the division then gives the IEEE result (a call, so that it is never
+    // evaluated on the common path)
+    if (__builtin_expect(!isfinite(q), 0)) return divide(b, t);
     return q;
 }
 
@@ -152,11 +153,11 @@ __device__ __forceinline__ void update_group(T (&b)[ROWS][RPW], const T *col,
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(Width<T>::THREADS, 1)
+template <typename T, int SLOTS>
+__global__ void __launch_bounds__(MAX_WARPS * 32, 1)
     panel_kernel(T *B, int64_t vstride, int64_t estride, int nvec, const Panel p)
 {
-    constexpr int RPW = Width<T>::RPW;
+    const int rpc = (blockDim.x >> 5) * RPW;   // right-hand sides of this CTA
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *bufs = reinterpret_cast<T *>(smem_raw);
     T *dgs = bufs + 2 * BUF;     // [2][CW] diagonal entries
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(Width<T>::THREADS, 1)
     T b[ROWS][RPW];
     int vec[RPW];
 #pragma unroll
-    for (int w = 0; w < RPW; ++w) vec[w] = blockIdx.x * RPC + warp * RPW + w;
+    for (int w = 0; w < RPW; ++w) vec[w] = blockIdx.x * rpc + warp * RPW + w;
 #pragma unroll
     for (int r = 0; r < ROWS; ++r)
 #pragma unroll
@@ -181,11 +182,11 @@ __global__ void __launch_bounds__(Width<T>::THREADS, 1)
         }
 
     {
-        Stage<T> st;
-        stage_load<T>(p, 0, 0, tid, st);
-        stage_store<T>(p, 0, 0, tid, st, bufs, dgs);
-        stage_load<T>(p, 0, HALF, tid, st);
-        stage_store<T>(p, 0, HALF, tid, st, bufs, dgs);
+        Stage<T, SLOTS> st;
+        stage_load<T, SLOTS>(p, 0, 0, tid, st);
+        stage_store<T, SLOTS>(p, 0, 0, tid, st, bufs, dgs);
+        stage_load<T, SLOTS>(p, 0, HALF, tid, st);
+        stage_store<T, SLOTS>(p, 0, HALF, tid, st, bufs, dgs);
     }
     // The groups run in a loop, not unrolled (the code stays small enough for the instruction
     // cache): the group being solved moves into cur[] and back; the later groups are
@@ -214,8 +215,8 @@ __global__ void __launch_bounds__(Width<T>::THREADS, 1)
             const bool more = d0 + CW < pw;   // a next chunk to stage meanwhile
             T *nbuf = bufs + ((ch + 1) & 1) * BUF;
             T *ndg = dgs + ((ch + 1) & 1) * CW;
-            Stage<T> st;
-            if (more) stage_load<T>(p, d0 + CW, 0, tid, st);
+            Stage<T, SLOTS> st;
+            if (more) stage_load<T, SLOTS>(p, d0 + CW, 0, tid, st);
             const int dn = min(CW, pw - d0);
             // the chunk's unknowns one after another; each updates only the later unknowns
             // of its own 32-row group here (the chain's latency is the solve's floor)
@@ -233,8 +234,8 @@ __global__ void __launch_bounds__(Width<T>::THREADS, 1)
                 }
             }
             if (more) {
-                stage_store<T>(p, d0 + CW, 0, tid, st, nbuf, ndg);
-                stage_load<T>(p, d0 + CW, HALF, tid, st);
+                stage_store<T, SLOTS>(p, d0 + CW, 0, tid, st, nbuf, ndg);
+                stage_load<T, SLOTS>(p, d0 + CW, HALF, tid, st);
             }
             // then the chunk's unknowns leave the later groups, in the same order (the
             // multiply-adds of every element still run in increasing column order), free of
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(Width<T>::THREADS, 1)
 #undef GFIP_TRSM_GROUP
             default: break;
             }
-            if (more) stage_store<T>(p, d0 + CW, HALF, tid, st, nbuf, ndg);
+            if (more) stage_store<T, SLOTS>(p, d0 + CW, HALF, tid, st, nbuf, ndg);
             __syncthreads();   // this buffer is restaged during the next chunk
             ++ch;
         }
@@ -299,24 +300,47 @@ cudaError_t launch_trsm_panel_impl(T *B, int64_t vstride, int64_t estride, int n
     if (pw > TRSM_PANEL) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            trsm::panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            static_cast<int>(trsm::smem_bytes<T>()));
-        if (e != cudaSuccess) return e;
+        for (auto *k : {trsm::panel_kernel<T, 1>, trsm::panel_kernel<T, 2>}) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(trsm::smem_bytes<T>()));
+            if (e != cudaSuccess) return e;
+        }
         configured = true;
     }
     trsm::Panel p;
+    // t(q, d): row index i and column index j of op(A) are k0 + r0 + sgn q and k0 + r0 + sgn d
+    // (swapped for side 'R'); op(A)[i, j] is element i + j lda ('N') or j + i lda ('T')
+    const int64_t ci = a_trans ? lda : 1, cj = a_trans ? 1 : lda;
+    p.cq = transpose_t ? cj : ci;
+    p.cd = transpose_t ? ci : cj;
+    p.sgn = lower_t ? 1 : -1;
+    p.o0 = (int64_t)(k0 + (lower_t ? 0 : pw - 1)) * (p.cq + p.cd);
     p.A = A;
-    p.lda = lda;
-    p.a_trans = a_trans;
-    p.transpose_t = transpose_t;
     p.lower_t = lower_t;
     p.unit = unit;
     p.k0 = k0;
     p.pw = pw;
-    const int blocks = (nvec + trsm::RPC - 1) / trsm::RPC;
-    trsm::panel_kernel<T><<<blocks, trsm::Width<T>::THREADS, trsm::smem_bytes<T>(), s>>>(
-        B, vstride, estride, nvec, p);
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int want = (nvec + sms * trsm::RPW - 1) / (sms * trsm::RPW);
+    const int warps = sizeof(T) == 4 ? trsm::MAX_WARPS
+                      : want < trsm::MIN_WARPS
+                          ? trsm::MIN_WARPS
+                          : (want > trsm::MAX_WARPS ? trsm::MAX_WARPS : want);
+    const int rpc = warps * trsm::RPW;
+    const int blocks = (nvec + rpc - 1) / rpc;
+    if (warps * 32 >= TRSM_PANEL)
+        trsm::panel_kernel<T, 1><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
+            B, vstride, estride, nvec, p);
+    else
+        trsm::panel_kernel<T, trsm::MAX_SLOTS><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
+            B, vstride, estride, nvec, p);
     return cudaGetLastError();
 }
 
