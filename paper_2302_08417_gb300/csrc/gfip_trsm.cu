@@ -19,12 +19,16 @@ namespace gfip {
 namespace trsm {
 
 // One right-hand side per warp: a warp's substitution chain is as short as it gets, and the
-// CTA's warps interleave their chains (two per warp measured 2.5 % slower at 2048 x 2048).
+// CTA's warps interleave their chains (two per warp, 8 warps a CTA, measured 11 % slower at
+// 2048 x 2048 in FP32).
 // FP32 CTAs run 16 warps.  FP64, bound by its DFMA pipe, runs between 8 and 16, as many as
 // spread the right-hand sides over all SMs (2048 of them on 152 SMs: 14 a CTA, 147 CTAs,
 // 11 % faster than 16 a CTA on 128 SMs; the same shape made FP32 5 % slower).
-constexpr int RPW = 1;
-constexpr int MIN_WARPS = 8, MAX_WARPS = 16;
+#ifndef GFIP_TRSM_RPW
+#define GFIP_TRSM_RPW 1
+#endif
+constexpr int RPW = GFIP_TRSM_RPW;   // (overridable at build time for measurements)
+constexpr int MIN_WARPS = 8 / RPW, MAX_WARPS = 16 / RPW;
 // loads a staging part takes a thread: one with 16 warps, two with fewer (the kernel is
 // compiled for both)
 constexpr int MAX_SLOTS = TRSM_PANEL / (MIN_WARPS * 32);
@@ -300,7 +304,8 @@ cudaError_t launch_trsm_panel_impl(T *B, int64_t vstride, int64_t estride, int n
     if (pw > TRSM_PANEL) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
-        for (auto *k : {trsm::panel_kernel<T, 1>, trsm::panel_kernel<T, 2>}) {
+        for (auto *k : {trsm::panel_kernel<T, 1>, trsm::panel_kernel<T, 2>,
+                        trsm::panel_kernel<T, trsm::MAX_SLOTS>}) {
             const cudaError_t e =
                 cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(trsm::smem_bytes<T>()));
@@ -337,6 +342,9 @@ cudaError_t launch_trsm_panel_impl(T *B, int64_t vstride, int64_t estride, int n
     const int blocks = (nvec + rpc - 1) / rpc;
     if (warps * 32 >= TRSM_PANEL)
         trsm::panel_kernel<T, 1><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
+            B, vstride, estride, nvec, p);
+    else if (warps * 64 >= TRSM_PANEL)
+        trsm::panel_kernel<T, 2><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
             B, vstride, estride, nvec, p);
     else
         trsm::panel_kernel<T, trsm::MAX_SLOTS><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
