@@ -945,6 +945,12 @@ def compact_summary(result) -> dict:
             f"{tag} {shape}": [v["fused"], v["fused_over_cublas"]]
             for tag in ("f64", "f32") for shape, v in ag.get(tag, {}).items()
             if "fused" in v}
+    ts = result.get("trsm")
+    if ts:
+        out["trsm:[fused_gflops,time_over_gemm]"] = {
+            f"{tag} {shape}": [v["fused"], v["trsm_time_over_gemm"]]
+            for tag in ("f64", "f32") for shape, v in ts.get(tag, {}).items()
+            if "fused" in v}
     return out
 
 
