@@ -35,7 +35,7 @@ def test_max_over_ranks_gloo_world2():
     world = 2
     elapsed = [1.25, 3.5]
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.start_processes(_rank_main, args=(world, port, elapsed, out), nprocs=world,
                            start_method="spawn", join=True)
