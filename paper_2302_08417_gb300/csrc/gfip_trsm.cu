@@ -29,101 +29,150 @@ namespace trsm {
 #endif
 constexpr int RPW = GFIP_TRSM_RPW;   // (overridable at build time for measurements)
 constexpr int MIN_WARPS = 8 / RPW, MAX_WARPS = 16 / RPW;
-// loads a staging part takes a thread: one with 16 warps, two with fewer (the kernel is
-// compiled for both)
+// staging slots a thread takes per half chunk: one with 16 warps, more with fewer (the
+// kernel is compiled for each)
 constexpr int MAX_SLOTS = TRSM_PANEL / (MIN_WARPS * 32);
 constexpr int ROWS = TRSM_PANEL / 32;     // 32-row groups of a panel: registers per vector
 constexpr int CW = 16;                    // triangle columns per staged chunk
-constexpr size_t BUF = (size_t)CW * TRSM_PANEL;   // elements of one chunk buffer
+constexpr int HALF = CW / 2;              // columns staged together
 static_assert(TRSM_PANEL % 32 == 0 && 32 % CW == 0, "a 32-row group is whole chunks");
 static_assert(ROWS == 16, "the group update below is written out for 16 groups");
+// A chunk buffer holds one row of CW triangle entries per unknown of the panel, rows padded to
+// PADW elements: a lane reads its row 16 bytes at a time, and the 8 lanes of one shared-memory
+// wavefront (rows 80 or 144 bytes apart) fall on distinct banks.
+template <typename T> __host__ __device__ constexpr int padw() { return CW + 16 / (int)sizeof(T); }
+template <typename T> __host__ __device__ constexpr size_t buf_elems() { return (size_t)TRSM_PANEL * padw<T>(); }
 // two chunk buffers, two diagonals and two reciprocal diagonals
-template <typename T> constexpr size_t smem_bytes() { return sizeof(T) * (2 * BUF + 4 * CW); }
+template <typename T> constexpr size_t smem_bytes() { return sizeof(T) * (2 * buf_elems<T>() + 4 * CW); }
+
+// 16-byte shared-memory accesses of a row (float4 / double2)
+__device__ __forceinline__ void ld16(const float *s, float (&v)[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(s);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld16(const double *s, double (&v)[2])
+{
+    const double2 t = *reinterpret_cast<const double2 *>(s);
+    v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void st16(float *s, const float *v)
+{
+    *reinterpret_cast<float4 *>(s) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st16(double *s, const double *v)
+{
+    *reinterpret_cast<double2 *>(s) = make_double2(v[0], v[1]);
+}
 
 // The panel's system in solve order: unknown q of the local lower triangular system is row
 // lower_t ? q : pw - 1 - q of the block, so an upper triangular block is solved by the same
 // forward loop.  t(r, c) = op(A)[k0 + r, k0 + c] (side 'L') or op(A)[k0 + c, k0 + r] (side
 // 'R', transpose_t), op(A)[i, j] = A[i + j lda] ('N') or A[j + i lda] ('T').  Every case is
-// linear in (q, d): t(q, d) sits at A[o0 + sgn (q cq + d cd)], the four numbers set on the
-// host (launch_trsm_panel).
+// linear in (q, d): t(q, d) sits at A0[q sq + d sd], the three set on the host
+// (launch_trsm_panel); one of |sq|, |sd| is 1.
 struct Panel {
-    const void *A;
-    int64_t o0, cq, cd;
-    int sgn;            // +1 lower, -1 upper (rows counted from the block's end)
+    const void *A0;
+    int64_t sq, sd;
+    int along_q;        // |sq| == 1: a column of the local system is contiguous
     int lower_t, unit;
-    int k0, pw;
+    int pw;
     __device__ __forceinline__ int row(int q) const { return lower_t ? q : pw - 1 - q; }
-    template <typename T> __device__ __forceinline__ const T *at(int q, int d) const
-    {
-        return static_cast<const T *>(A) + o0 + sgn * ((int64_t)q * cq + (int64_t)d * cd);
-    }
-    // along q the copies run along memory (|cq| == 1)
-    __device__ __forceinline__ bool along_q() const { return cq == 1; }
 };
 
-// Staging of chunk [d0, d0 + CW) of the strictly lower part of the local system:
-// buf[dd * TRSM_PANEL + q] = t(q, d0 + dd) for q > d0 + dd, zero elsewhere (rows from the
-// chunk's 32-row group on), and its diagonal (unless unit).  A chunk is CW parts: where A is
-// contiguous along q a part is one column of the chunk, otherwise a slice of its rows, so
-// that a warp's loads are consecutive in A either way; a part is at most SLOTS elements per
-// thread.  Plain loads into registers, issued a chunk ahead and stored to shared memory
-// after the work they hide behind (element copies through cp.async cost more issue slots).
-constexpr int HALF = CW / 2;   // parts loaded together
+// Staging of chunk [d0, d0 + CW) of the strictly lower part of the local system: row q of
+// the buffer holds t(q, d0 + dd) at buf[q PADW + dd] for q > d0 + dd, zero elsewhere, for the
+// rows of the chunk's 32-row group and after (qlo <= q < qhi), and the chunk's diagonal
+// (unless unit) with its reciprocals.  A chunk is staged in two halves of HALF columns,
+// each a half's loads into registers issued ahead of the work they hide behind and stored to
+// shared memory after it.  Where columns are contiguous in A (along_q) a thread stages rows
+// (q = qlo + tid + i NT) and stores each row's half with 16-byte stores; otherwise a thread
+// keeps one column (dd = tid % CW) and stages every (NT / CW)-th row, so that a warp's loads
+// run along A's rows either way.  A warp whose rows all lie past qhi skips its slot.
 template <typename T, int SLOTS> struct Stage {
-    T v[HALF][SLOTS];
+    T v[SLOTS][HALF];
     T diag;
 };
 
-template <typename T>
-__device__ __forceinline__ void stage_slot(const Panel &p, int d0, int part, int i, int tid,
-                                           int &q, int &dd)
+template <int SLOTS>
+__device__ __forceinline__ int stage_row(const Panel &p, int qlo, int hf, int i, int j, int e)
 {
-    const int qlo = d0 & ~31, qhi = (p.pw + 31) & ~31;
-    const int e = tid + blockDim.x * i;
-    if (p.along_q()) {
-        dd = part;
-        q = qlo + e;
-        if (q >= qhi) q = -1;
-    } else {
-        const int rows = (qhi - qlo) / CW;
-        dd = e % CW;
-        const int qo = e / CW;
-        q = qo < rows ? qlo + part * rows + qo : -1;
-    }
+    // row of slot (i, j) of half hf for thread e (e = tid, or tid & ~31 for the warp's first)
+    const int nt = blockDim.x;
+    if (p.along_q) return qlo + e + i * nt;
+    return qlo + e / CW + ((hf * HALF + j) * SLOTS + i) * (nt / CW);
 }
 
 template <typename T, int SLOTS>
-__device__ __forceinline__ void stage_load(const Panel &p, int d0, int part0, int tid,
+__device__ __forceinline__ void stage_load(const Panel &p, int d0, int hf, int tid,
                                            Stage<T, SLOTS> &st)
 {
-#pragma unroll
-    for (int k = 0; k < HALF; ++k)
+    const T *A0 = static_cast<const T *>(p.A0);
+    const int qlo = d0 & ~31, qhi = (p.pw + 31) & ~31, pw = p.pw;
+    const int wfirst = tid & ~31;
+    if (p.along_q) {
 #pragma unroll
         for (int i = 0; i < SLOTS; ++i) {
-            int q, dd;
-            stage_slot<T>(p, d0, part0 + k, i, tid, q, dd);
-            const int d = d0 + dd;
-            st.v[k][i] = (q > d && q < p.pw) ? *p.at<T>(q, d) : T(0);
+            if (stage_row<SLOTS>(p, qlo, hf, i, 0, wfirst) >= qhi) continue;   // warp-uniform
+            const int q = stage_row<SLOTS>(p, qlo, hf, i, 0, tid);
+            const int da = d0 + hf * HALF;
+            const T *src = A0 + (int64_t)q * p.sq + (int64_t)da * p.sd;
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) {
+                st.v[i][j] = (q > da + j && q < pw) ? *src : T(0);
+                src += p.sd;
+            }
         }
-    if (part0 == 0 && tid < CW) {
+    } else {
+        const int d = d0 + (tid % CW);
+#pragma unroll
+        for (int j = 0; j < HALF; ++j)
+#pragma unroll
+            for (int i = 0; i < SLOTS; ++i) {
+                if (stage_row<SLOTS>(p, qlo, hf, i, j, wfirst) >= qhi) continue;
+                const int q = stage_row<SLOTS>(p, qlo, hf, i, j, tid);
+                st.v[i][j] = (q > d && q < pw) ? A0[(int64_t)q * p.sq + (int64_t)d * p.sd] : T(0);
+            }
+    }
+    if (hf == 0 && tid < CW) {
         const int d = d0 + tid;
-        st.diag = (!p.unit && d < p.pw) ? *p.at<T>(d, d) : T(1);
+        st.diag = (!p.unit && d < pw) ? A0[(int64_t)d * (p.sq + p.sd)] : T(1);
     }
 }
 
 template <typename T, int SLOTS>
-__device__ __forceinline__ void stage_store(const Panel &p, int d0, int part0, int tid,
-                                            const Stage<T, SLOTS> &st, T *buf, T *dg)
+__device__ __forceinline__ void stage_store(const Panel &p, int d0, int hf, int tid,
+                                            const Stage<T, SLOTS> &st, T *buf, T *dg, T *dr)
 {
-#pragma unroll
-    for (int k = 0; k < HALF; ++k)
+    constexpr int PADW = padw<T>(), V = 16 / (int)sizeof(T);
+    const int qlo = d0 & ~31, qhi = (p.pw + 31) & ~31;
+    const int wfirst = tid & ~31;
+    if (p.along_q) {
 #pragma unroll
         for (int i = 0; i < SLOTS; ++i) {
-            int q, dd;
-            stage_slot<T>(p, d0, part0 + k, i, tid, q, dd);
-            if (q >= 0) buf[dd * TRSM_PANEL + q] = st.v[k][i];
+            if (stage_row<SLOTS>(p, qlo, hf, i, 0, wfirst) >= qhi) continue;
+            const int q = stage_row<SLOTS>(p, qlo, hf, i, 0, tid);
+            if (q < qhi) {
+                T *row = buf + q * PADW + hf * HALF;
+#pragma unroll
+                for (int j = 0; j < HALF; j += V) st16(row + j, &st.v[i][j]);
+            }
         }
-    if (part0 == 0 && tid < CW) dg[tid] = st.diag;
+    } else {
+        const int dd = tid % CW;
+#pragma unroll
+        for (int j = 0; j < HALF; ++j)
+#pragma unroll
+            for (int i = 0; i < SLOTS; ++i) {
+                if (stage_row<SLOTS>(p, qlo, hf, i, j, wfirst) >= qhi) continue;
+                const int q = stage_row<SLOTS>(p, qlo, hf, i, j, tid);
+                if (q < qhi) buf[q * PADW + dd] = st.v[i][j];
+            }
+    }
+    if (hf == 0 && tid < CW) {
+        dg[tid] = st.diag;
+        dr[tid] = p.unit ? T(1) : T(1) / st.diag;
+    }
 }
 
 // b / t from r = RN(1 / t): the product corrected by one exact residual step (an FMA gives
@@ -143,17 +192,22 @@ template <typename T> __device__ __forceinline__ T quotient(T b, T t, T r)
 }
 
 // b[R][w] -= sum over the chunk's columns dd, in order, of t(32 R + lane, d0 + dd) x[dd][w]:
-// this lane's element of group R of every right-hand side (col = the chunk's staged column 0
-// at the group's first row).
+// this lane's element of group R of every right-hand side (row = this lane's buffer row in
+// group 0), the row read 16 bytes at a time.
 template <typename T, int R, int RPW>
-__device__ __forceinline__ void update_group(T (&b)[ROWS][RPW], const T *col,
+__device__ __forceinline__ void update_group(T (&b)[ROWS][RPW], const T *row,
                                              const T (&x)[CW][RPW])
 {
+    constexpr int PADW = padw<T>(), V = 16 / (int)sizeof(T);
+    const T *r = row + 32 * R * PADW;
 #pragma unroll
-    for (int dd = 0; dd < CW; ++dd) {
-        const T tq = col[dd * TRSM_PANEL];
+    for (int d4 = 0; d4 < CW; d4 += V) {
+        T t[V];
+        ld16(r + d4, t);
 #pragma unroll
-        for (int w = 0; w < RPW; ++w) b[R][w] = fma(-tq, x[dd][w], b[R][w]);
+        for (int j = 0; j < V; ++j)
+#pragma unroll
+            for (int w = 0; w < RPW; ++w) b[R][w] = fma(-t[j], x[d4 + j][w], b[R][w]);
     }
 }
 
@@ -161,6 +215,8 @@ template <typename T, int SLOTS>
 __global__ void __launch_bounds__(MAX_WARPS * 32, 1)
     panel_kernel(T *B, int64_t vstride, int64_t estride, int nvec, const Panel p)
 {
+    constexpr int PADW = padw<T>(), V = 16 / (int)sizeof(T);
+    constexpr size_t BUF = buf_elems<T>();
     const int rpc = (blockDim.x >> 5) * RPW;   // right-hand sides of this CTA
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *bufs = reinterpret_cast<T *>(smem_raw);
@@ -188,13 +244,14 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1)
     {
         Stage<T, SLOTS> st;
         stage_load<T, SLOTS>(p, 0, 0, tid, st);
-        stage_store<T, SLOTS>(p, 0, 0, tid, st, bufs, dgs);
-        stage_load<T, SLOTS>(p, 0, HALF, tid, st);
-        stage_store<T, SLOTS>(p, 0, HALF, tid, st, bufs, dgs);
+        stage_store<T, SLOTS>(p, 0, 0, tid, st, bufs, dgs, drs);
+        stage_load<T, SLOTS>(p, 0, 1, tid, st);
+        stage_store<T, SLOTS>(p, 0, 1, tid, st, bufs, dgs, drs);
     }
     // The groups run in a loop, not unrolled (the code stays small enough for the instruction
     // cache): the group being solved moves into cur[] and back; the later groups are
-    // updated in an unrolled loop over all groups, skipping the ones not after it.
+    // updated through a switch that enters at the first of them.  One barrier a chunk: the
+    // one that publishes chunk ch also ends every warp's reads of the buffer restaged next.
     int ch = 0;   // chunks begun
 #pragma unroll 1
     for (int r = 0; r < ROWS; ++r) {
@@ -206,40 +263,56 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1)
 #pragma unroll
                 for (int w = 0; w < RPW; ++w) cur[w] = b[rr][w];
             }
+        const T *lrow = nullptr;   // this lane's row of group 0 in the current buffer
 #pragma unroll 1
         for (int h = 0; h < 32 / CW; ++h) {
             const int d0 = 32 * r + h * CW;
             if (d0 >= pw) break;
             __syncthreads();      // chunk ch is in shared memory
             const T *tb = bufs + (ch & 1) * BUF;
-            const T *dg = dgs + (ch & 1) * CW;
-            T *dr = drs + (ch & 1) * CW;
-            if (tid < CW) dr[tid] = p.unit ? T(1) : T(1) / dg[tid];
-            __syncthreads();
+            const T *dg = dgs + (ch & 1) * CW, *dr = drs + (ch & 1) * CW;
+            lrow = tb + lane * PADW;
             const bool more = d0 + CW < pw;   // a next chunk to stage meanwhile
             T *nbuf = bufs + ((ch + 1) & 1) * BUF;
-            T *ndg = dgs + ((ch + 1) & 1) * CW;
+            T *ndg = dgs + ((ch + 1) & 1) * CW, *ndr = drs + ((ch + 1) & 1) * CW;
             Stage<T, SLOTS> st;
             if (more) stage_load<T, SLOTS>(p, d0 + CW, 0, tid, st);
             const int dn = min(CW, pw - d0);
+            // this lane's row of the chunk (its entries left of the diagonal: FP32 reads it
+            // whole ahead of the chain, FP64, short of registers, an entry a step), and, for
+            // the lane whose unknown is in the chunk, its diagonal entry and reciprocal
+            const int ln = lane - h * CW;   // this lane's unknown within the chunk, if in range
+            const T *crow = lrow + 32 * r * PADW;
+            constexpr bool PRELOAD = sizeof(T) == 4;
+            T trow[CW];
+            if (PRELOAD) {
+#pragma unroll
+                for (int d4 = 0; d4 < CW; d4 += V) {
+                    T v[V];
+                    ld16(crow + d4, v);
+#pragma unroll
+                    for (int j = 0; j < V; ++j) trow[d4 + j] = v[j];
+                }
+            }
+            const int lc = ln < 0 ? 0 : (ln >= CW ? CW - 1 : ln);
+            const T t = dg[lc], rt = dr[lc];
             // the chunk's unknowns one after another; each updates only the later unknowns
             // of its own 32-row group here (the chain's latency is the solve's floor)
-            for (int dd = 0; dd < dn; ++dd) {
-                const int owner = h * CW + dd;   // the lane holding unknown d0 + dd
-                const T t = dg[dd], rt = dr[dd];
-                const T tq = tb[dd * TRSM_PANEL + 32 * r + lane];
+#pragma unroll
+            for (int dd = 0; dd < CW; ++dd) {
+                if (dd >= dn) break;
 #pragma unroll
                 for (int w = 0; w < RPW; ++w) {
                     T bc = cur[w];
-                    if (!p.unit && lane == owner) bc = quotient(bc, t, rt);
-                    const T x = __shfl_sync(0xffffffffu, bc, owner);
-                    if (lane == owner) cur[w] = x;
-                    if (lane > owner) cur[w] = fma(-tq, x, cur[w]);
+                    if (!p.unit && ln == dd) bc = quotient(bc, t, rt);
+                    const T x = __shfl_sync(0xffffffffu, bc, h * CW + dd);
+                    if (ln == dd) cur[w] = x;
+                    if (ln > dd) cur[w] = fma(-(PRELOAD ? trow[dd] : crow[dd]), x, cur[w]);
                 }
             }
             if (more) {
-                stage_store<T, SLOTS>(p, d0 + CW, 0, tid, st, nbuf, ndg);
-                stage_load<T, SLOTS>(p, d0 + CW, HALF, tid, st);
+                stage_store<T, SLOTS>(p, d0 + CW, 0, tid, st, nbuf, ndg, ndr);
+                stage_load<T, SLOTS>(p, d0 + CW, 1, tid, st);
             }
             // then the chunk's unknowns leave the later groups, in the same order (the
             // multiply-adds of every element still run in increasing column order), free of
@@ -257,11 +330,10 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1)
                     const T x = __shfl_sync(0xffffffffu, cur[w], h * CW + dd);
                     xs[dd][w] = dd < dn ? x : T(0);
                 }
-            const T *col = tb + lane;
             switch (r) {
 #define GFIP_TRSM_GROUP(R)                                                                  \
     case R - 1:                                                                             \
-        if (32 * R < pw) update_group<T, R, RPW>(b, col + 32 * R, xs);                     \
+        if (32 * R < pw) update_group<T, R, RPW>(b, lrow, xs);                              \
         [[fallthrough]];
                 GFIP_TRSM_GROUP(1) GFIP_TRSM_GROUP(2) GFIP_TRSM_GROUP(3)
                 GFIP_TRSM_GROUP(4) GFIP_TRSM_GROUP(5) GFIP_TRSM_GROUP(6)
@@ -271,8 +343,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1)
 #undef GFIP_TRSM_GROUP
             default: break;
             }
-            if (more) stage_store<T, SLOTS>(p, d0 + CW, HALF, tid, st, nbuf, ndg);
-            __syncthreads();   // this buffer is restaged during the next chunk
+            if (more) stage_store<T, SLOTS>(p, d0 + CW, 1, tid, st, nbuf, ndg, ndr);
             ++ch;
         }
 #pragma unroll
@@ -317,14 +388,14 @@ cudaError_t launch_trsm_panel_impl(T *B, int64_t vstride, int64_t estride, int n
     // t(q, d): row index i and column index j of op(A) are k0 + r0 + sgn q and k0 + r0 + sgn d
     // (swapped for side 'R'); op(A)[i, j] is element i + j lda ('N') or j + i lda ('T')
     const int64_t ci = a_trans ? lda : 1, cj = a_trans ? 1 : lda;
-    p.cq = transpose_t ? cj : ci;
-    p.cd = transpose_t ? ci : cj;
-    p.sgn = lower_t ? 1 : -1;
-    p.o0 = (int64_t)(k0 + (lower_t ? 0 : pw - 1)) * (p.cq + p.cd);
-    p.A = A;
+    const int64_t cq = transpose_t ? cj : ci, cd = transpose_t ? ci : cj;
+    const int sgn = lower_t ? 1 : -1;
+    p.A0 = A + (int64_t)(k0 + (lower_t ? 0 : pw - 1)) * (cq + cd);
+    p.sq = sgn * cq;
+    p.sd = sgn * cd;
+    p.along_q = cq == 1;
     p.lower_t = lower_t;
     p.unit = unit;
-    p.k0 = k0;
     p.pw = pw;
     static int sms = 0;
     if (sms == 0) {
