@@ -294,20 +294,62 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1)
                     for (int j = 0; j < V; ++j) trow[d4 + j] = v[j];
                 }
             }
+            const bool inch = ln >= 0 && ln < CW;
             const int lc = ln < 0 ? 0 : (ln >= CW ? CW - 1 : ln);
             const T t = dg[lc], rt = dr[lc];
             // the chunk's unknowns one after another; each updates only the later unknowns
-            // of its own 32-row group here (the chain's latency is the solve's floor)
+            // of its own 32-row group here (the chain's latency is the solve's floor).
+            // A whole chunk first takes the short form: every lane forms the quotient of its
+            // own element (by its own diagonal entry; lanes outside the chunk, and a unit
+            // diagonal, by 1), the owner's is broadcast, and every lane subtracts its multiple
+            // with its row's entry, which is zero on and above the diagonal, so that the
+            // chunk's unknowns keep their last right-hand side and take their quotient once
+            // the chunk is done (the one the owner broadcast: the same operands).  A
+            // non-finite quotient in any lane makes the chunk run again in the exact form
+            // below (owner-only quotients, the division for special values), as does a short
+            // last chunk.  With finite values both forms give the same bits.  FP64 keeps the
+            // exact form: its extra multiply-adds would load the DFMA pipe that bounds it.
+            bool exact = sizeof(T) == 8 || dn < CW;
+            if (!exact) {
+                const T tl = inch ? t : T(1), rl = inch ? rt : T(1);
+                T cur0[RPW];
+                T acc = T(0);   // stays zero while every quotient is finite
 #pragma unroll
-            for (int dd = 0; dd < CW; ++dd) {
-                if (dd >= dn) break;
+                for (int w = 0; w < RPW; ++w) cur0[w] = cur[w];
 #pragma unroll
-                for (int w = 0; w < RPW; ++w) {
-                    T bc = cur[w];
-                    if (!p.unit && ln == dd) bc = quotient(bc, t, rt);
-                    const T x = __shfl_sync(0xffffffffu, bc, h * CW + dd);
-                    if (ln == dd) cur[w] = x;
-                    if (ln > dd) cur[w] = fma(-(PRELOAD ? trow[dd] : crow[dd]), x, cur[w]);
+                for (int dd = 0; dd < CW; ++dd)
+#pragma unroll
+                    for (int w = 0; w < RPW; ++w) {
+                        const T q0 = cur[w] * rl;
+                        const T qv = fma(fma(-tl, q0, cur[w]), rl, q0);
+                        acc = fma(qv, T(0), acc);
+                        const T x = __shfl_sync(0xffffffffu, qv, h * CW + dd);
+                        cur[w] = fma(-(PRELOAD ? trow[dd] : crow[dd]), x, cur[w]);
+                    }
+                if (__any_sync(0xffffffffu, !(acc == T(0)))) {
+                    exact = true;
+#pragma unroll
+                    for (int w = 0; w < RPW; ++w) cur[w] = cur0[w];
+                } else if (inch) {
+#pragma unroll
+                    for (int w = 0; w < RPW; ++w) {
+                        const T q0 = cur[w] * rl;
+                        cur[w] = fma(fma(-tl, q0, cur[w]), rl, q0);
+                    }
+                }
+            }
+            if (exact) {
+#pragma unroll
+                for (int dd = 0; dd < CW; ++dd) {
+                    if (dd >= dn) break;
+#pragma unroll
+                    for (int w = 0; w < RPW; ++w) {
+                        T bc = cur[w];
+                        if (!p.unit && ln == dd) bc = quotient(bc, t, rt);
+                        const T x = __shfl_sync(0xffffffffu, bc, h * CW + dd);
+                        if (ln == dd) cur[w] = x;
+                        if (ln > dd) cur[w] = fma(-(PRELOAD ? trow[dd] : crow[dd]), x, cur[w]);
+                    }
                 }
             }
             if (more) {
