@@ -18,20 +18,18 @@
 namespace gfip {
 namespace trsm {
 
-// One right-hand side per warp: a warp's substitution chain is as short as it gets, and the
-// CTA's warps interleave their chains (two per warp, 8 warps a CTA, measured 11 % slower at
-// 2048 x 2048 in FP32).
-// FP32 CTAs run 16 warps.  FP64, bound by its DFMA pipe, runs between 8 and 16, as many as
-// spread the right-hand sides over all SMs (2048 of them on 152 SMs: 14 a CTA, 147 CTAs,
-// 11 % faster than 16 a CTA on 128 SMs; the same shape made FP32 5 % slower).
-#ifndef GFIP_TRSM_RPW
-#define GFIP_TRSM_RPW 1
-#endif
-constexpr int RPW = GFIP_TRSM_RPW;   // (overridable at build time for measurements)
-constexpr int MIN_WARPS = 8 / RPW, MAX_WARPS = 16 / RPW;
-// staging slots a thread takes per half chunk: one with 16 warps, more with fewer (the
-// kernel is compiled for each)
-constexpr int MAX_SLOTS = TRSM_PANEL / (MIN_WARPS * 32);
+// Right-hand sides per warp: FP32 two (8 warps a CTA: the two chains interleave within the
+// warp; 6 % faster at 2048 x 2048 than one a warp in 16 warps), FP64 one (its registers do
+// not hold two, and it is bound by its DFMA pipe): the shortest chain per right-hand side.
+// FP64 runs between 8 and 16 warps a CTA, as many as spread the right-hand sides over all SMs
+// (2048 of them on 152 SMs: 14 a CTA, 147 CTAs, 11 % faster than 16 a CTA on 128 SMs).
+template <typename T> struct Shape {
+    static constexpr int RPW = sizeof(T) == 4 ? 2 : 1;
+    static constexpr int MIN_WARPS = 8 / RPW, MAX_WARPS = 16 / RPW;
+    // staging slots a thread takes per half chunk: one with 512 threads, more with fewer
+    // (the kernel is compiled for each)
+    static constexpr int MAX_SLOTS = TRSM_PANEL / (MIN_WARPS * 32);
+};
 constexpr int ROWS = TRSM_PANEL / 32;     // 32-row groups of a panel: registers per vector
 constexpr int CW = 16;                    // triangle columns per staged chunk
 constexpr int HALF = CW / 2;              // columns staged together
@@ -212,9 +210,10 @@ __device__ __forceinline__ void update_group(T (&b)[ROWS][RPW], const T *row,
 }
 
 template <typename T, int SLOTS>
-__global__ void __launch_bounds__(MAX_WARPS * 32, 1)
+__global__ void __launch_bounds__(Shape<T>::MAX_WARPS * 32, 1)
     panel_kernel(T *B, int64_t vstride, int64_t estride, int nvec, const Panel p)
 {
+    constexpr int RPW = Shape<T>::RPW;
     constexpr int PADW = padw<T>(), V = 16 / (int)sizeof(T);
     constexpr size_t BUF = buf_elems<T>();
     const int rpc = (blockDim.x >> 5) * RPW;   // right-hand sides of this CTA
@@ -415,10 +414,11 @@ cudaError_t launch_trsm_panel_impl(T *B, int64_t vstride, int64_t estride, int n
 {
     if (nvec <= 0 || pw <= 0) return cudaSuccess;
     if (pw > TRSM_PANEL) return cudaErrorInvalidValue;
+    using S = trsm::Shape<T>;
     static bool configured = false;
     if (!configured) {
         for (auto *k : {trsm::panel_kernel<T, 1>, trsm::panel_kernel<T, 2>,
-                        trsm::panel_kernel<T, trsm::MAX_SLOTS>}) {
+                        trsm::panel_kernel<T, S::MAX_SLOTS>}) {
             const cudaError_t e =
                 cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(trsm::smem_bytes<T>()));
@@ -446,12 +446,11 @@ cudaError_t launch_trsm_panel_impl(T *B, int64_t vstride, int64_t estride, int n
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
-    const int want = (nvec + sms * trsm::RPW - 1) / (sms * trsm::RPW);
-    const int warps = sizeof(T) == 4 ? trsm::MAX_WARPS
-                      : want < trsm::MIN_WARPS
-                          ? trsm::MIN_WARPS
-                          : (want > trsm::MAX_WARPS ? trsm::MAX_WARPS : want);
-    const int rpc = warps * trsm::RPW;
+    const int want = (nvec + sms * S::RPW - 1) / (sms * S::RPW);
+    const int warps = sizeof(T) == 4 ? S::MAX_WARPS
+                      : want < S::MIN_WARPS ? S::MIN_WARPS
+                                            : (want > S::MAX_WARPS ? S::MAX_WARPS : want);
+    const int rpc = warps * S::RPW;
     const int blocks = (nvec + rpc - 1) / rpc;
     if (warps * 32 >= TRSM_PANEL)
         trsm::panel_kernel<T, 1><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
@@ -460,7 +459,7 @@ cudaError_t launch_trsm_panel_impl(T *B, int64_t vstride, int64_t estride, int n
         trsm::panel_kernel<T, 2><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
             B, vstride, estride, nvec, p);
     else
-        trsm::panel_kernel<T, trsm::MAX_SLOTS><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
+        trsm::panel_kernel<T, S::MAX_SLOTS><<<blocks, warps * 32, trsm::smem_bytes<T>(), s>>>(
             B, vstride, estride, nvec, p);
     return cudaGetLastError();
 }
