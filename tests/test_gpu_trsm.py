@@ -163,6 +163,51 @@ def test_integer_unit_exact_and_policies(runner, side, uplo, ta):
         assert np.array_equal(X.view(np.uint8), first.view(np.uint8))
 
 
+def ieee_class(x):
+    """0 NaN, 1 +inf, 2 -inf, 3 finite, element by element."""
+    return np.select([np.isnan(x), np.isposinf(x), np.isneginf(x)], [0, 1, 2], 3)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("uplo,ta", list(itertools.product("LU", "NT")))
+def test_special_values_follow_ieee(runner, dtype, uplo, ta):
+    """A zero on the diagonal (unknown 300 of 600), a NaN (column 0) and an infinity (column 1)
+    in B: every element of X is NaN, +inf, -inf or finite exactly where the oracle's
+    substitution puts one (which of the four a sum of infinities gives depends only on the
+    signs of its terms, not on the order it is summed in), and the finite elements agree with
+    the oracle's.  The solve meets the special values part-way through a panel, in chunks
+    where every quotient is finite, in chunks where one is not, and in the short chunk that
+    ends the 88-unknown second panel."""
+    rng = np.random.Generator(np.random.PCG64(29))
+    m, n = 600, 48
+    lda, ldb = m + 3, m + 5
+    A = system(rng, m, lda, uplo, "N", dtype)
+    B0 = inputs.colmajor(rng, m, n, ldb, dtype)
+    B0[5] = np.nan
+    B0[200 + ldb] = np.inf
+    # which infinity 1/0 gives follows the sign of the residual that meets the zero: with a 1
+    # there instead, that residual is the solution's element, well away from zero here
+    A1 = A.astype(np.float64)
+    A1[300 + 300 * lda] = 1.0
+    s = inputs.as_matrix(oracle.trsm_result("L", uplo, ta, "N", m, n, 1.0, A1, lda,
+                                            B0.astype(np.float64), ldb), m, n, ldb)[300]
+    assert np.all(np.abs(s[np.isfinite(s)]) > 1e-3)
+    A[300 + 300 * lda] = 0.0
+    X, guard = run(runner, "L", uplo, ta, "N", m, n, 1.0, A, lda, B0, ldb)
+    assert np.all(np.isnan(guard))
+    ref = oracle.trsm_result("L", uplo, ta, "N", m, n, 1.0, A.astype(np.float64), lda,
+                             B0.astype(np.float64), ldb)
+    got = inputs.as_matrix(X.astype(np.float64), m, n, ldb)
+    want = inputs.as_matrix(ref, m, n, ldb)
+    assert np.array_equal(ieee_class(got), ieee_class(want))
+    fin = np.isfinite(want)
+    assert fin.any() and not fin.all()
+    u = inputs.unit_roundoff(dtype)
+    scale = np.where(fin, np.abs(want), 0.0).max(axis=0, keepdims=True)
+    err = np.abs(np.where(fin, got, 0.0) - np.where(fin, want, 0.0))
+    assert np.all(err <= 64 * (m + 64) * u * scale)
+
+
 def test_alpha_zero_and_codes(runner):
     m, n = 40, 30
     X, _ = run(runner, "R", "L", "T", "N", m, n, 0.0, np.full(n * n, np.nan), n,
