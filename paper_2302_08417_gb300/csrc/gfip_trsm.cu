@@ -6,9 +6,9 @@
 // solved.  The kernel solves a panel by column-oriented substitution: once unknown d is known
 // (divided by its diagonal entry), every unknown below it loses its multiple at once; per
 // chunk of columns the chain updates only its own 32-row group, and the later groups are
-// updated afterwards, off the chain.  A warp holds one right-hand side, one element per lane
-// and 32-row group, in registers; the panel's triangle streams through shared memory in
-// chunks of columns, double-buffered and shared by the CTA's warps, the next chunk loaded
+// updated afterwards, off the chain.  A warp holds one or two right-hand sides, one element
+// per lane and 32-row group, in registers; the panel's triangle streams through shared memory
+// in chunks of columns, double-buffered and shared by the CTA's warps, the next chunk loaded
 // into registers while this one is solved.  Only the entries a triangular solve reads are
 // read: never the other triangle, nor a unit diagonal.
 #include <cstdint>
